@@ -1,0 +1,151 @@
+/*
+ * fp.h - C ABI of the GB300 free-stream-preserving (FP) upwind finite-difference
+ * residual library (libfpgb300.so).
+ *
+ * Method: Su, Cai, Pan & Hu, "Reformulated dissipation for the free-stream
+ * preserving of the conservative finite difference schemes on curvilinear grids",
+ * arXiv 2101.05886.  The library advances the compressible Euler equations on
+ * stationary curvilinear grids (Sec. 2.1, Eq. NS without the viscous terms).  At
+ * every cell face it forms the reference face state Q* (Eq. Q_star), subtracts
+ * the reference flux from every cell value of the upwind stencil, reconstructs
+ * with unmodified WENO5-JS or linear upwind under characteristic local
+ * Lax-Friedrichs splitting, adds back the metric-weighted reference flux
+ * (Eqs. my_point1 to my_point3) and differences the face fluxes into the
+ * residual (Eq. aderivative).  Time integration is third-order TVD Runge-Kutta.
+ *
+ * Conventions for every entry point
+ *  - Plain C types only.  No C++ type or exception crosses this boundary, and
+ *    nothing here calls exit() or abort().
+ *  - Pointers named *_dev are CUDA device pointers.  Pointers named *_host are
+ *    host pointers.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Calls are stream-ordered and asynchronous unless stated.
+ *  - State layout: conserved variables (rho, rho u, rho v, rho w, rho E) as a
+ *    C-contiguous array [5][nk][nj][ni] (i fastest) of interior points only.
+ *    The element type is double for FP_F64 and float for FP_F32_MIXED.  Ghost
+ *    values come from the boundary codes when they are read; they are never
+ *    stored.  The caller owns every state and output buffer.
+ *  - Errors: every call returns an fp_status.  FP_ERR_ARG means the call was
+ *    rejected before any GPU work was queued.  FP_ERR_CUDA reports a CUDA error,
+ *    which may come from earlier asynchronous work.  fp_last_error() gives a
+ *    one-line message for the last failing call on a context.
+ *  - A context is not thread-safe: use it from one host thread at a time.
+ */
+#ifndef FP_GB300_H
+#define FP_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FP_OK = 0,
+  FP_ERR_ARG = 1,          /* invalid argument, nothing was queued */
+  FP_ERR_CUDA = 2,         /* CUDA runtime error (possibly from earlier async work) */
+  FP_ERR_OOM = 3,          /* device allocation failed */
+  FP_ERR_NONFINITE = 4,    /* a kernel produced a non-finite state value */
+  FP_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  FP_ERR_UNSUPPORTED = 6   /* valid but not implemented combination */
+} fp_status;
+
+enum { FP_WENO5_JS = 0, FP_LINEAR_UPWIND5 = 1 };            /* reconstruction, Sec. 2.2.2 */
+enum { FP_F64 = 0, FP_F32_MIXED = 1 };                      /* precision of the sweep */
+enum { FP_BC_PERIODIC = 0, FP_BC_FARFIELD = 1, FP_BC_EXTRAP = 2 };
+enum { FP_XI = 0, FP_ETA = 1, FP_ZETA = 2 };
+
+typedef struct {
+  int dims;                   /* 2 or 3 */
+  int n[3];                   /* solution points ni, nj, nk (nk = 1 when dims == 2) */
+  int metric_order;           /* M in {2,4,6,8}: order of metrics, Jacobian and every
+                                 face interpolation (Sec. 3 Eq. metric_discret, Remark 3) */
+  int scheme;                 /* FP_WENO5_JS or FP_LINEAR_UPWIND5 */
+  int free_stream_preserving; /* 1 = the paper's FP face flux, 0 = plain scheme (control) */
+  int characteristic;         /* 1 = Roe characteristic-wise splitting (paper), 0 = component-wise */
+  int precision;              /* FP_F64, or FP_F32_MIXED: metrics built in FP64, sweep in FP32 */
+  int bc[3][2];               /* per direction (lo, hi): FP_BC_PERIODIC | FP_BC_FARFIELD | FP_BC_EXTRAP */
+  double gamma;               /* ratio of specific heats (Sec. 2.1 Eq. EOS: 1.4) */
+  double q_inf[5];            /* far-field state; also the reference state of the FP32 form */
+} fp_grid_desc;
+
+typedef struct fp_ctx fp_ctx;
+typedef struct fp_batch fp_batch;
+
+/* Ghost width G = max(3, M/2) of the stored metrics. */
+int fp_ghost_width(int metric_order);
+/* Node ghost layers required by fp_init_grid: G + 3M/2 (the metric products,
+   the metrics and the Jacobian are all formed by the same order-M central
+   operator, so every cell a stencil can reach satisfies the discrete surface
+   conservation law, Sec. 2.1 Eq. SCL). */
+int fp_node_ghost_width(int metric_order);
+
+/* Build a block: copies the node coordinates to the device and forms, in FP64,
+   the symmetric conservative metrics (Eq. JBabc), the Jacobian (Eq. JB), the
+   face metrics of every direction (Eq. xidJ at order M) and the work lists.
+   xyz_nodes_host: double [dims][nk+2g][nj+2g][ni+2g] (2-D: [2][nj+2g][ni+2g]),
+   g = ghost_nodes >= fp_node_ghost_width(M); read during the call only.
+   Allocates device memory owned by the context.  Synchronises `stream`. */
+int fp_init_grid(const fp_grid_desc *desc, const double *xyz_nodes_host, int ghost_nodes,
+                 void *stream, fp_ctx **out);
+
+/* dqdt_dev = -J * sum_d (F'_{d,i+1/2} - F'_{d,i-1/2}) (Eq. aderivative, Delta xi = 1).
+   q_dev is read only; dqdt_dev has the state layout and type.  Uses the
+   context's residual scratch. */
+int fp_rhs(fp_ctx *ctx, const void *q_dev, void *dqdt_dev, void *stream);
+
+/* One third-order TVD Runge-Kutta step (Gottlieb & Shu) of size dt, in place on
+   q_dev.  Uses the context's two stage buffers and residual scratch.  A stage
+   whose updated state is not finite sets a device flag that fp_get_device_status()
+   reports. */
+int fp_rk3_step(fp_ctx *ctx, void *q_dev, double dt, void *stream);
+
+/* dt = cfl / max over points of sum_d (|U_d| + c |grad d|), grad d = J (d_x, d_y, d_z)/J.
+   Synchronises `stream` to return the value in *dt_out (host). */
+int fp_cfl_dt(fp_ctx *ctx, const void *q_dev, double cfl, double *dt_out, void *stream);
+
+/* Copy the stored cell metrics to host memory: double [10][nk+2G][nj+2G][ni+2G]
+   (2-D: [10][1][nj+2G][ni+2G]); entry 3d+a is (d-th coordinate)_{x_a}/J, entry 9
+   is 1/J.  Values are those the sweep uses (rounded to float for FP_F32_MIXED). */
+int fp_get_metrics(fp_ctx *ctx, double *host_out);
+
+/* Copy the face metrics of direction dir to host memory: double [3][faces], faces
+   ordered like the state with n_dir+1 faces along dir (face f+1/2, f = -1..n-1). */
+int fp_get_face_metrics(fp_ctx *ctx, int dir, double *host_out);
+
+/* Synchronise `stream`, read and clear the device status word (non-finite state,
+   bounded-wait timeout).  Returns FP_OK, FP_ERR_NONFINITE or FP_ERR_TIMEOUT. */
+int fp_get_device_status(fp_ctx *ctx, void *stream);
+
+/* Number of kernel launches one fp_rhs / fp_rk3_step call queues. */
+int fp_launches_per_rhs(const fp_ctx *ctx);
+int fp_launches_per_step(const fp_ctx *ctx);
+
+/* Tile shape used for direction dir: faces per chunk and lines per tile. */
+int fp_get_tile(const fp_ctx *ctx, int dir, int *faces, int *lines);
+/* Override the tile shape (faces in {8,16,32}, faces*lines == 256). */
+int fp_set_tile(fp_ctx *ctx, int dir, int faces, int lines);
+
+const char *fp_last_error(const fp_ctx *ctx);
+const char *fp_status_string(int status);
+void fp_free(fp_ctx *ctx);                 /* NULL-safe; synchronises the device */
+
+/* ---------------- batched multi-block advance ----------------
+   A batch advances many independent blocks (same precision, scheme, metric order)
+   together: one persistent launch per direction pass covers the work of every
+   block, the three RK stages are captured once into a CUDA graph, and each call
+   replays it.  The batch keeps pointers to the contexts (they must outlive it)
+   and to the caller's state buffers q_devs[b] given at creation.  When autotune
+   is nonzero, fp_batch_create times each candidate tile shape on the blocks and
+   keeps the fastest per size class; it may run kernels on the blocks' buffers. */
+int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int autotune,
+                    void *stream, fp_batch **out);
+/* One RK3 step of size dt on every block (graph replay). */
+int fp_batch_rk3_step(fp_batch *batch, double dt, void *stream);
+/* dqdt for every block (no graph); dqdt_devs[b] has block b's state layout. */
+int fp_batch_rhs(fp_batch *batch, void *const *dqdt_devs, void *stream);
+int fp_batch_launches_per_step(const fp_batch *batch);
+const char *fp_batch_last_error(const fp_batch *batch);
+void fp_batch_free(fp_batch *batch);       /* NULL-safe */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FP_GB300_H */

@@ -1,0 +1,57 @@
+/*
+ * oracle.h - plain, serial, FP64 CPU reference of the free-stream-preserving (FP)
+ * upwind conservative finite-difference residual of Su, Cai, Pan & Hu,
+ * "Reformulated dissipation for the free-stream preserving of the conservative
+ * finite difference schemes on curvilinear grids" (arXiv 2101.05886).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark load this library.  It shares no code, header,
+ * table or helper with the CUDA library; the two are compared on the same seeded
+ * inputs.
+ *
+ * Layouts (all C order, i fastest, float64):
+ *   nodes : [dims][nk+2Gn][nj+2Gn][ni+2Gn]   (2-D: [2][nj+2Gn][ni+2Gn])
+ *   met   : [10][nk+2G][nj+2G][ni+2G]         (2-D: [10][1][nj+2G][ni+2G])
+ *           entry 3*d+a = (d-th curvilinear coordinate)_(x_a) / J, entry 9 = 1/J
+ *   q, R  : [5][nk][nj][ni]  conserved variables (rho, rho u, rho v, rho w, rho E)
+ * with G = max(3, M/2) and Gn >= G + 3M/2.
+ */
+#ifndef FP_ORACLE_H
+#define FP_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int dims;        /* 2 or 3 */
+  int n[3];        /* ni, nj, nk (nk = 1 in 2-D) */
+  int M;           /* metric and face-interpolation order: 2, 4, 6 or 8 */
+  int scheme;      /* 0 = WENO5-JS, 1 = 5th-order linear upwind */
+  int fp;          /* 1 = free-stream-preserving form, 0 = plain scheme */
+  int charwise;    /* 1 = characteristic-wise (Roe eigenvectors), 0 = component-wise */
+  int form;        /* 2 = WENO(F_m - F*_m + F*_face) (Eq. my_point2), 1 = WENO(F_m - F*_m) + F*_face (Eq. my_point1) */
+  int bc[3][2];    /* 0 periodic, 1 far field (q_inf), 2 zero gradient */
+  double gamma;
+  double qinf[5];
+} or_cfg;
+
+int or_ghost(int M);                 /* G = max(3, M/2) */
+int or_node_ghost(int M);            /* G + 3M/2 */
+void or_interp_coef(int M, double c[8]);      /* face interpolation weights (Sec. 3) */
+double or_weno5(const double v[5]);           /* WENO5-JS of v[0..4] = f_{i-2..i+2} at i+1/2 */
+double or_lu5(const double v[5]);             /* linear upwind 5 = WENO with optimal weights */
+void or_eigensystem(const double qL[5], const double qR[5], const double k[3], double gamma,
+                    double L[25], double R[25]);
+int or_metrics(const or_cfg *c, const double *nodes, int Gn, double *met);
+/* face flux at i+1/2 from 8 consecutive cells i-3..i+4 along one direction d:
+   q8 [8][5], met8 [8][4] = (k_x, k_y, k_z, 1/J) of that direction */
+void or_face_flux(const or_cfg *c, const double q8[40], const double met8[32], double out[5]);
+int or_rhs(const or_cfg *c, const double *met, const double *q, double *R, double *dqdt);
+int or_rk3_step(const or_cfg *c, const double *met, double *q, double dt);
+double or_cfl_dt(const or_cfg *c, const double *met, const double *q, double cfl);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
