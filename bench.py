@@ -1,0 +1,318 @@
+"""Benchmark of the free-stream-preserving residual sweep on GB300.
+
+Default workload: 64 blocks of seeded uneven sizes (each side U{32..128}; half
+cylinder O-grids, half periodic wavy grids), Mach 3 stream with a 1e-3 smooth
+perturbation, WENO5-JS FP form, 6th-order metrics, FP32 state and arithmetic on
+FP64-built metrics, all blocks advanced by one CUDA-graph replay per SSP-RK3
+step (one persistent launch per direction pass), autotuned tiles.
+
+Metric: Mcell-RHS/s per RK stage = interior points x RK stages / second.
+Prints one JSON line (rank 0).  --impl reference times the serial FP64 oracle
+on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-RHS/s per RK stage"
+WORKLOAD = "batched multi-block: 64 blocks U{32..128}^3 (32 cylinder O-grids, 32 wavy), Mach 3 + 1e-3 perturbation, WENO5-JS FP, M6 metrics"
+CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+# Algorithmic bytes per interior point per RK stage of the FP32 form:
+# state: read Q^(s) 20 + read Q^n (stages 2,3 only: 2/3 * 20) + write Q^(s+1) 20;
+# cell metrics 9 + 1/J as float 40; face metrics 3 directions x 3 floats 36.
+BYTES_PER_CELL_STAGE_F32 = 20 + 20 * 2.0 / 3.0 + 20 + 40 + 36
+BYTES_PER_CELL_STAGE_F64 = 2 * BYTES_PER_CELL_STAGE_F32
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_gpu(args):
+    import torch
+    from paper_2101_05886_gb300 import binding as B
+    from paper_2101_05886_gb300 import inputs as I
+    from paper_2101_05886_gb300.solver import Batch, Block
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    M = 6
+    Gn = B.fp_node_ghost_width(M)
+    qinf = I.uniform_qinf(3.0, 0.0)
+    prec = B.FP_F32_MIXED
+    sizes = I.batched_block_sizes(64, 32, 128, 4)
+    rng = np.random.default_rng(1004)
+    blocks, states = [], []
+    for k, n in enumerate(sizes):
+        g = (I.cylinder_ogrid(n, Lz=float(rng.uniform(1.0, 8.0)), Gn=Gn) if k < 32
+             else I.periodic_wavy_3d(n, L=10.0, amp=0.08, Gn=Gn))
+        blk = Block(g, metric_order=M, precision=prec, q_inf=qinf)
+        q = blk.to_device(I.perturbed_state(g, qinf, amp=1e-3, seed=k))
+        blk.grid = None
+        blocks.append(blk)
+        states.append(q)
+    ncells = sum(int(np.prod(n)) for n in sizes)
+    batch = Batch(blocks, states, autotune=True)
+    dt = min(b.cfl_dt(q, 0.5) for b, q in zip(blocks, states))
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.rk3_step(dt)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gstart = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    gend = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s in range(args.steps):
+            gstart[s].record(stream)
+            batch.rk3_step(dt)
+            gend[s].record(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    graph_ms = sum(a.elapsed_time(b) for a, b in zip(gstart, gend))
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    stages = 3 * args.steps
+    value = world * ncells * stages / (ms * 1e-3) / 1e6
+    launches_per_step = batch.launches_per_step()
+    st = [b.status() for b in blocks]
+    assert all(s == B.FP_OK for s in st), "non-finite state during the benchmark"
+
+    # ---- end-to-end through the public API with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        hosts = [torch.empty(q.shape, dtype=q.dtype, pin_memory=True) for q in states]
+        for h, q in zip(hosts, states):
+            h.copy_(q)
+        h2d = sum(h.numel() * h.element_size() for h in hosts)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            for h, q in zip(hosts, states):
+                q.copy_(h, non_blocking=True)
+            batch.rk3_step(dt)
+            for h, q in zip(hosts, states):
+                h.copy_(q, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ems = f0.elapsed_time(f1)
+        if world > 1:
+            t = torch.tensor([ems], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = t.item()
+        e2e = {"value": world * ncells * stages / (ems * 1e-3) / 1e6, "unit": "Mcell/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d}
+
+    # ---- roofline of the dominant kernel (the sweep; every launch in the graph is one)
+    hbm, src = peaks()
+    per_launch_ms = graph_ms / (args.steps * launches_per_step)
+    alg_bytes_per_launch = BYTES_PER_CELL_STAGE_F32 * ncells / 3.0     # one of the 3 direction passes
+    achieved = alg_bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
+            "kernel": "fpk::fp_sweep<float,6,0>", "launch_ms": round(per_launch_ms, 4)}
+
+    # ---- FP64 plain single block (256^3 wavy grid + vortex) on the same GPU
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        g = I.periodic_wavy_3d((256, 256, 256), L=10.0, amp=0.08, Gn=Gn)
+        b64 = Block(g, metric_order=M, precision=B.FP_F64, q_inf=I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0))
+        q64 = b64.to_device(I.vortex_3d(g, mach=0.8, eps=5.0, L=10.0))
+        del g
+        dt64 = b64.cfl_dt(q64, 0.5)
+        b64.rk3_step(q64, dt64)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n64 = 2
+        h0.record(stream)
+        for _ in range(n64):
+            b64.rk3_step(q64, dt64)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = h0.elapsed_time(h1)
+        fp64 = {"workload": "single block 256^3 wavy grid, Mach 0.8 + vortex, WENO5-JS FP, M6",
+                "value": 256 ** 3 * 3 * n64 / (ms64 * 1e-3) / 1e6, "unit": "Mcell/s",
+                "ms_per_step": ms64 / n64, "dtype": "f64"}
+        b64.close()
+
+    result = None
+    if rank == 0:
+        cpu = None if args.no_cpu else cpu_baseline(args)
+        result = {
+            "metric": METRIC, "value": round(value, 2), "unit": "Mcell/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded grids and states)",
+            "config": {"workload": WORKLOAD, "blocks": 64, "cells_per_gpu": ncells,
+                       "rk_stages_per_step": 3, "precision": "FP32 sweep on FP64-built metrics",
+                       "parallelism": f"independent block batches per GPU x{world}",
+                       "l2": "inputs larger than L2 (state %.0f MB)" % (ncells * 20 / 1e6)},
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "fp64_plain_single_block": fp64,
+        }
+        print(json.dumps(result))
+    for b in blocks:
+        b.close()
+    batch.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _oracle_sample(seconds_target=10.0, n=40):
+    """The oracle on a bounded sample of the workload: one O-grid block of n^3
+    points from the batch's family, RK3 steps until about `seconds_target` s."""
+    import oracle as O
+    from paper_2101_05886_gb300 import inputs as I
+    M = 6
+    g = I.cylinder_ogrid((n, n, n), Lz=4.0, Gn=O.node_ghost(M))
+    qinf = I.uniform_qinf(3.0, 0.0)
+    cfg = O.cfg_for(g, M=M, qinf=qinf)
+    met = O.metrics(cfg, g.nodes, g.Gn)
+    q = I.perturbed_state(g, qinf, amp=1e-3, seed=0)
+    dt = O.cfl_dt(cfg, met, q, 0.5)
+    return cfg, met, q, dt, n ** 3
+
+
+def cpu_baseline(args):
+    import oracle as O
+    cfg, met, q, dt, ncell = _oracle_sample()
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        q = O.rk3_step(cfg, met, q, dt)
+        steps += 1
+        if time.perf_counter() - t0 > 10.0:
+            break
+    el = time.perf_counter() - t0
+    return {"value": round(ncell * 3 * steps / el / 1e6, 4), "unit": "Mcell/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} RK3 steps of one 40^3 cylinder O-grid block (Mach 3 + 1e-3 perturbation, WENO5-JS FP, M6), serial FP64 C"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle as O
+    cfg, met, q, dt, ncell = _oracle_sample(n=24)
+    for _ in range(args.warmup):
+        q = O.rk3_step(cfg, met, q, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q = O.rk3_step(cfg, met, q, dt)
+    el = time.perf_counter() - t0
+    v = ncell * 3 * args.steps / el / 1e6
+    sample = f"each step one RK3 step of one 24^3 cylinder O-grid block of the workload's family, serial FP64 C oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Mcell/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded grids and states)", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": round(v, 4), "unit": "Mcell/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(v, 4), "unit": "Mcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,672 @@
+// api.cu - C ABI of libfpgb300.so (declared in include/fp.h): block contexts,
+// residual and Runge-Kutta drivers, the batched multi-block advance captured in a
+// CUDA graph, and the tile autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fp.h"
+#include "fp_internal.h"
+
+using fpk::BlockDev;
+using fpk::DirDev;
+
+struct fp_ctx {
+  fp_grid_desc desc;
+  int G = 0;
+  int is_f32 = 0;
+  size_t esize = 8;
+  long long ncells = 0;
+  long long nmet = 0;                 // points of one metric component (ghosted box)
+  long long nface[3] = {0, 0, 0};     // faces per direction
+  void *met = nullptr;                // T [10][nmet]
+  void *fmet[3] = {nullptr, nullptr, nullptr};
+  void *q1 = nullptr, *q2 = nullptr, *racc = nullptr;
+  int *status = nullptr;
+  double *dt_dev = nullptr;
+  unsigned long long *cfl_bits = nullptr;
+  BlockDev hblk;
+  BlockDev *dblk = nullptr;
+  BlockDev uploaded;                  // last BlockDev copied to dblk
+  std::vector<int2> hitems[3];
+  int2 *items[3] = {nullptr, nullptr, nullptr};
+  int nitems[3] = {0, 0, 0};
+  int per_sm = 1;
+  int nsm = 152;
+  double dt_host = 0.0;
+  std::string err;
+};
+
+struct fp_batch {
+  std::vector<fp_ctx *> ctx;
+  std::vector<BlockDev> hblk;
+  BlockDev *dblk = nullptr;
+  int2 *items[3] = {nullptr, nullptr, nullptr};
+  int nitems[3] = {0, 0, 0};
+  double *dt_dev = nullptr;
+  double dt_host = 0.0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int dims = 3, M = 6, scheme = 0, charwise = 1, fp = 1, is_f32 = 1;
+  int per_sm = 1, nsm = 152;
+  std::string err;
+};
+
+namespace {
+
+int fail(fp_ctx *c, int st, const std::string &msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+int cuda_fail(fp_ctx *c, cudaError_t e, const char *where) {
+  if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA;
+}
+
+int bfail(fp_batch *b, int st, const std::string &msg) {
+  if (b) b->err = msg;
+  return st;
+}
+
+int ghost_of(int M) { return std::max(3, M / 2); }
+
+int prepare(int is_f32, int M, int scheme) {
+  return is_f32 ? fpk::prepare_sweep_f32(M, scheme) : fpk::prepare_sweep_f64(M, scheme);
+}
+
+cudaError_t launch(int is_f32, const fpk::SweepLaunch &L, int M, int scheme, int charwise, int fp,
+                   cudaStream_t s) {
+  return is_f32 ? fpk::launch_sweep_f32(L, M, scheme, charwise, fp, s)
+                : fpk::launch_sweep_f64(L, M, scheme, charwise, fp, s);
+}
+
+void default_tile(int dir, int nd, int *S, int *TT) {
+  (void)nd;
+  if (dir == 0) { *S = 32; *TT = 8; }
+  else { *S = 8; *TT = 32; }
+}
+
+void fill_dirs(fp_ctx *c) {
+  const int ni = c->desc.n[0], nj = c->desc.n[1], nk = c->desc.n[2], G = c->G;
+  const int dims = c->desc.dims;
+  const long long qs1 = ni, qs2 = (long long)ni * nj;
+  const long long ei = ni + 2 * G, ej = nj + 2 * G;
+  const long long ms1 = ei, ms2 = ei * ej;
+  BlockDev &B = c->hblk;
+  // direction 0: lines along i, transverse (j, k)
+  {
+    DirDev &D = B.dir[0];
+    D.nd = ni; D.nt1 = nj; D.nlines = (long long)nj * nk;
+    D.qT1 = qs1; D.qT2 = qs2; D.qsd = 1;
+    D.mT1 = ms1; D.mT2 = ms2; D.msd = 1;
+    D.fT1 = ni + 1; D.fT2 = (long long)(ni + 1) * nj; D.fsd = 1;
+  }
+  // direction 1: lines along j, transverse (i, k)
+  {
+    DirDev &D = B.dir[1];
+    D.nd = nj; D.nt1 = ni; D.nlines = (long long)ni * nk;
+    D.qT1 = 1; D.qT2 = qs2; D.qsd = qs1;
+    D.mT1 = 1; D.mT2 = ms2; D.msd = ms1;
+    D.fT1 = 1; D.fT2 = (long long)ni * (nj + 1); D.fsd = ni;
+  }
+  // direction 2: lines along k, transverse (i, j)
+  {
+    DirDev &D = B.dir[2];
+    D.nd = nk; D.nt1 = ni; D.nlines = (long long)ni * nj;
+    D.qT1 = 1; D.qT2 = qs1; D.qsd = qs2;
+    D.mT1 = 1; D.mT2 = ms1; D.msd = ms2;
+    D.fT1 = 1; D.fT2 = ni; D.fsd = (long long)ni * nj;
+  }
+  for (int d = 0; d < 3; ++d) {
+    DirDev &D = B.dir[d];
+    D.fc = c->nface[d];
+    D.bclo = c->desc.bc[d][0];
+    D.bchi = c->desc.bc[d][1];
+    D.fmet = c->fmet[d];
+    if (d < dims) default_tile(d, D.nd, &D.S, &D.TT);
+    else { D.S = 8; D.TT = 32; D.nlines = 0; }
+  }
+  B.dims = dims;
+  B.G = G;
+  B.qc = (long long)ni * nj * nk;
+  B.mc = c->nmet;
+  B.moff = G + G * ms1 + (dims == 3 ? G * ms2 : 0);
+  B.met = c->met;
+  B.q[0] = nullptr; B.q[1] = c->q1; B.q[2] = c->q2;
+  B.racc = c->racc;
+  B.dqdt = nullptr;
+  for (int v = 0; v < 5; ++v) B.qbar[v] = c->desc.q_inf[v];
+  B.gamma = c->desc.gamma;
+  B.status = c->status;
+}
+
+void make_items(const BlockDev &B, int bidx, int d, std::vector<int2> &out) {
+  const DirDev &D = B.dir[d];
+  for (long long L0 = 0; L0 < D.nlines; L0 += D.TT) out.push_back(make_int2(bidx, (int)L0));
+}
+
+int upload_items(fp_ctx *c) {
+  for (int d = 0; d < 3; ++d) {
+    if (c->items[d]) { cudaFree(c->items[d]); c->items[d] = nullptr; }
+    c->hitems[d].clear();
+    if (d < c->desc.dims) make_items(c->hblk, 0, d, c->hitems[d]);
+    c->nitems[d] = (int)c->hitems[d].size();
+    if (c->nitems[d] == 0) continue;
+    cudaError_t e = cudaMalloc(&c->items[d], c->hitems[d].size() * sizeof(int2));
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(items)");
+    e = cudaMemcpy(c->items[d], c->hitems[d].data(), c->hitems[d].size() * sizeof(int2),
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy(items)");
+  }
+  return FP_OK;
+}
+
+int sync_block(fp_ctx *c, cudaStream_t s) {
+  if (std::memcmp(&c->uploaded, &c->hblk, sizeof(BlockDev)) == 0) return FP_OK;
+  cudaError_t e = cudaMemcpyAsync(c->dblk, &c->hblk, sizeof(BlockDev), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "upload block descriptor");
+  c->uploaded = c->hblk;
+  return FP_OK;
+}
+
+int grid_for(int per_sm, int nsm, int nitems) {
+  long long g = (long long)per_sm * nsm;
+  if (g > nitems) g = nitems;
+  return g < 1 ? 1 : (int)g;
+}
+
+int validate(const fp_grid_desc *d, int ghost_nodes, std::string &why) {
+  if (!d) { why = "desc is NULL"; return 0; }
+  if (d->dims != 2 && d->dims != 3) { why = "dims must be 2 or 3"; return 0; }
+  const int M = d->metric_order;
+  if (M != 2 && M != 4 && M != 6 && M != 8) { why = "metric_order must be 2, 4, 6 or 8"; return 0; }
+  const int G = ghost_of(M);
+  for (int k = 0; k < 3; ++k) {
+    if (d->n[k] < 1) { why = "n must be positive"; return 0; }
+    if (k < d->dims && d->n[k] < G) { why = "each swept extent must be at least the ghost width"; return 0; }
+    if (k < d->dims && (long long)d->n[k] > (1LL << 20)) { why = "extent too large"; return 0; }
+  }
+  if (d->dims == 2 && d->n[2] != 1) { why = "n[2] must be 1 in 2-D"; return 0; }
+  if ((long long)d->n[0] * d->n[1] * d->n[2] > (1LL << 31) - 1) { why = "too many points"; return 0; }
+  if (d->scheme != FP_WENO5_JS && d->scheme != FP_LINEAR_UPWIND5) { why = "unknown scheme"; return 0; }
+  if (d->precision != FP_F64 && d->precision != FP_F32_MIXED) { why = "unknown precision"; return 0; }
+  if (d->free_stream_preserving != 0 && d->free_stream_preserving != 1) { why = "free_stream_preserving must be 0 or 1"; return 0; }
+  if (d->characteristic != 0 && d->characteristic != 1) { why = "characteristic must be 0 or 1"; return 0; }
+  for (int k = 0; k < d->dims; ++k)
+    for (int s = 0; s < 2; ++s)
+      if (d->bc[k][s] < 0 || d->bc[k][s] > 2) { why = "unknown boundary code"; return 0; }
+  if (!(d->gamma > 1.0) || !std::isfinite(d->gamma)) { why = "gamma must exceed 1"; return 0; }
+  const double rho = d->q_inf[0];
+  if (!(rho > 0.0)) { why = "q_inf density must be positive"; return 0; }
+  double ke = 0.5 * (d->q_inf[1] * d->q_inf[1] + d->q_inf[2] * d->q_inf[2] + d->q_inf[3] * d->q_inf[3]) / rho;
+  if (!((d->gamma - 1.0) * (d->q_inf[4] - ke) > 0.0)) { why = "q_inf pressure must be positive"; return 0; }
+  if (ghost_nodes < G + 3 * (M / 2)) { why = "ghost_nodes below fp_node_ghost_width(metric_order)"; return 0; }
+  return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fp_ghost_width(int metric_order) { return ghost_of(metric_order); }
+int fp_node_ghost_width(int metric_order) { return ghost_of(metric_order) + 3 * (metric_order / 2); }
+
+const char *fp_status_string(int st) {
+  switch (st) {
+    case FP_OK: return "ok";
+    case FP_ERR_ARG: return "invalid argument";
+    case FP_ERR_CUDA: return "CUDA error";
+    case FP_ERR_OOM: return "device out of memory";
+    case FP_ERR_NONFINITE: return "non-finite state";
+    case FP_ERR_TIMEOUT: return "device wait timed out";
+    case FP_ERR_UNSUPPORTED: return "unsupported combination";
+    default: return "unknown status";
+  }
+}
+
+const char *fp_last_error(const fp_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void fp_free(fp_ctx *c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  cudaFree(c->met);
+  for (int d = 0; d < 3; ++d) { cudaFree(c->fmet[d]); cudaFree(c->items[d]); }
+  cudaFree(c->q1); cudaFree(c->q2); cudaFree(c->racc);
+  cudaFree(c->status); cudaFree(c->dt_dev); cudaFree(c->cfl_bits); cudaFree(c->dblk);
+  delete c;
+}
+
+int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, void *stream,
+                 fp_ctx **out) {
+  if (!out) return FP_ERR_ARG;
+  *out = nullptr;
+  std::string why;
+  if (!validate(desc, ghost_nodes, why) || !xyz) return FP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  fp_ctx *c = new fp_ctx();
+  std::memset(&c->hblk, 0, sizeof(BlockDev));
+  std::memset(&c->uploaded, 0xff, sizeof(BlockDev));
+  c->desc = *desc;
+  const int dims = desc->dims, M = desc->metric_order;
+  c->G = ghost_of(M);
+  c->is_f32 = desc->precision == FP_F32_MIXED;
+  c->esize = c->is_f32 ? sizeof(float) : sizeof(double);
+  const int *n = desc->n;
+  c->ncells = (long long)n[0] * n[1] * n[2];
+  const int G = c->G, Gn = ghost_nodes, h = M / 2;
+  auto ext = [&](int d, int g) -> long long { return d < dims ? n[d] + 2LL * g : 1LL; };
+  const long long nnode = ext(0, Gn) * ext(1, Gn) * ext(2, Gn);
+  const long long nb1 = ext(0, G + M) * ext(1, G + M) * ext(2, G + M);
+  const long long nb2 = ext(0, G + h) * ext(1, G + h) * ext(2, G + h);
+  c->nmet = ext(0, G) * ext(1, G) * ext(2, G);
+  for (int d = 0; d < 3; ++d)
+    c->nface[d] = d < dims ? c->ncells / n[d] * (n[d] + 1) : 0;
+
+  cudaError_t e;
+  double *nodes = nullptr, *met64 = nullptr, *scratch = nullptr, *fm64[3] = {nullptr, nullptr, nullptr};
+  auto cleanup_tmp = [&]() {
+    cudaFree(nodes); cudaFree(scratch);
+    if (c->is_f32) { cudaFree(met64); for (int d = 0; d < 3; ++d) cudaFree(fm64[d]); }
+  };
+#define FP_TRY(call, where)                         \
+  do {                                              \
+    e = (call);                                     \
+    if (e != cudaSuccess) {                         \
+      int st = cuda_fail(c, e, where);              \
+      cleanup_tmp();                                \
+      std::fprintf(stderr, "fp_init_grid: %s\n", c->err.c_str()); \
+      fp_free(c);                                   \
+      return st;                                    \
+    }                                               \
+  } while (0)
+  int dev = 0;
+  FP_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+  FP_TRY(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+  FP_TRY(cudaMalloc(&nodes, (size_t)dims * nnode * sizeof(double)), "cudaMalloc(nodes)");
+  FP_TRY(cudaMemcpyAsync(nodes, xyz, (size_t)dims * nnode * sizeof(double), cudaMemcpyHostToDevice, s),
+         "copy nodes");
+  FP_TRY(cudaMalloc(&met64, (size_t)10 * c->nmet * sizeof(double)), "cudaMalloc(metrics)");
+  for (int d = 0; d < dims; ++d)
+    FP_TRY(cudaMalloc(&fm64[d], (size_t)3 * c->nface[d] * sizeof(double)), "cudaMalloc(face metrics)");
+  FP_TRY(cudaMalloc(&scratch, (size_t)9 * (nb1 + nb2) * sizeof(double)), "cudaMalloc(metric scratch)");
+  fpk::MetricJob J;
+  J.dims = dims; J.M = M; J.G = G; J.Gn = Gn;
+  for (int d = 0; d < 3; ++d) { J.n[d] = n[d]; J.fmet[d] = fm64[d]; }
+  J.nodes = nodes; J.met = met64; J.scratch = scratch;
+  FP_TRY(fpk::build_metrics(J, s), "build metrics");
+  if (c->is_f32) {
+    FP_TRY(cudaMalloc(&c->met, (size_t)10 * c->nmet * sizeof(float)), "cudaMalloc(metrics f32)");
+    FP_TRY(fpk::convert_f64_to_f32(met64, (float *)c->met, 10 * c->nmet, s), "convert metrics");
+    for (int d = 0; d < dims; ++d) {
+      FP_TRY(cudaMalloc(&c->fmet[d], (size_t)3 * c->nface[d] * sizeof(float)), "cudaMalloc(face f32)");
+      FP_TRY(fpk::convert_f64_to_f32(fm64[d], (float *)c->fmet[d], 3 * c->nface[d], s), "convert face metrics");
+    }
+  } else {
+    c->met = met64;
+    for (int d = 0; d < 3; ++d) c->fmet[d] = fm64[d];
+  }
+  FP_TRY(cudaStreamSynchronize(s), "metric construction");
+  cleanup_tmp();
+  nodes = nullptr; scratch = nullptr;
+  if (c->is_f32) { met64 = nullptr; for (int d = 0; d < 3; ++d) fm64[d] = nullptr; }
+  const size_t sbytes = (size_t)5 * c->ncells * c->esize;
+  FP_TRY(cudaMalloc(&c->q1, sbytes), "cudaMalloc(stage 1)");
+  FP_TRY(cudaMalloc(&c->q2, sbytes), "cudaMalloc(stage 2)");
+  FP_TRY(cudaMalloc(&c->racc, sbytes), "cudaMalloc(residual)");
+  FP_TRY(cudaMalloc(&c->status, sizeof(int)), "cudaMalloc(status)");
+  FP_TRY(cudaMemset(c->status, 0, sizeof(int)), "clear status");
+  FP_TRY(cudaMalloc(&c->dt_dev, sizeof(double)), "cudaMalloc(dt)");
+  FP_TRY(cudaMalloc(&c->cfl_bits, sizeof(unsigned long long)), "cudaMalloc(cfl)");
+  FP_TRY(cudaMalloc(&c->dblk, sizeof(BlockDev)), "cudaMalloc(block)");
+  fill_dirs(c);
+  c->per_sm = prepare(c->is_f32, M, desc->scheme);
+  FP_TRY(cudaGetLastError(), "prepare sweep kernels");
+  int st = upload_items(c);
+  if (st != FP_OK) { fp_free(c); return st; }
+#undef FP_TRY
+  *out = c;
+  return FP_OK;
+}
+
+static int run_passes(fp_ctx *c, int rk, cudaStream_t s) {
+  const int dims = c->desc.dims, M = c->desc.metric_order;
+  for (int stage = 0; stage < (rk ? 3 : 1); ++stage) {
+    for (int d = 0; d < dims; ++d) {
+      fpk::SweepLaunch L;
+      L.blocks = c->dblk;
+      L.items = c->items[d];
+      L.nitems = c->nitems[d];
+      L.dir = d;
+      L.mode = d == 0 ? fpk::MODE_WRITE : (d == dims - 1 ? (rk ? fpk::MODE_RK : fpk::MODE_RHS) : fpk::MODE_ADD);
+      L.stage = stage;
+      L.dt = c->dt_dev;
+      L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
+      cudaError_t e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic,
+                             c->desc.free_stream_preserving, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
+    }
+  }
+  return FP_OK;
+}
+
+int fp_rhs(fp_ctx *c, const void *q, void *dqdt, void *stream) {
+  if (!c) return FP_ERR_ARG;
+  if (!q || !dqdt) return fail(c, FP_ERR_ARG, "fp_rhs: null buffer");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->hblk.q[0] = const_cast<void *>(q);
+  c->hblk.dqdt = dqdt;
+  int st = sync_block(c, s);
+  if (st) return st;
+  return run_passes(c, 0, s);
+}
+
+int fp_rk3_step(fp_ctx *c, void *q, double dt, void *stream) {
+  if (!c) return FP_ERR_ARG;
+  if (!q) return fail(c, FP_ERR_ARG, "fp_rk3_step: null state");
+  if (!std::isfinite(dt)) return fail(c, FP_ERR_ARG, "fp_rk3_step: dt not finite");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->hblk.q[0] = q;
+  int st = sync_block(c, s);
+  if (st) return st;
+  c->dt_host = dt;
+  cudaError_t e = cudaMemcpyAsync(c->dt_dev, &c->dt_host, sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "upload dt");
+  return run_passes(c, 1, s);
+}
+
+int fp_cfl_dt(fp_ctx *c, const void *q, double cfl, double *dt_out, void *stream) {
+  if (!c) return FP_ERR_ARG;
+  if (!q || !dt_out || !(cfl > 0.0)) return fail(c, FP_ERR_ARG, "fp_cfl_dt: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  c->hblk.q[0] = const_cast<void *>(q);
+  int st = sync_block(c, s);
+  if (st) return st;
+  cudaError_t e = cudaMemsetAsync(c->cfl_bits, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cfl clear");
+  e = fpk::launch_cfl(c->dblk, c->is_f32, c->ncells, c->desc.n, c->desc.dims, c->cfl_bits, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cfl launch");
+  unsigned long long bits = 0;
+  e = cudaMemcpyAsync(&bits, c->cfl_bits, sizeof(bits), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cfl readback");
+  double mx;
+  std::memcpy(&mx, &bits, sizeof(mx));
+  if (!(mx > 0.0) || !std::isfinite(mx)) return fail(c, FP_ERR_NONFINITE, "fp_cfl_dt: spectral radius not positive");
+  *dt_out = cfl / mx;
+  return FP_OK;
+}
+
+int fp_get_metrics(fp_ctx *c, double *host_out) {
+  if (!c) return FP_ERR_ARG;
+  if (!host_out) return fail(c, FP_ERR_ARG, "fp_get_metrics: null output");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "fp_get_metrics");
+  const long long n = 10 * c->nmet;
+  if (c->is_f32) {
+    std::vector<float> tmp(n);
+    e = cudaMemcpy(tmp.data(), c->met, n * sizeof(float), cudaMemcpyDeviceToHost);
+    for (long long i = 0; i < n; ++i) host_out[i] = tmp[i];
+  } else {
+    e = cudaMemcpy(host_out, c->met, n * sizeof(double), cudaMemcpyDeviceToHost);
+  }
+  return e == cudaSuccess ? FP_OK : cuda_fail(c, e, "fp_get_metrics copy");
+}
+
+int fp_get_face_metrics(fp_ctx *c, int dir, double *host_out) {
+  if (!c) return FP_ERR_ARG;
+  if (!host_out || dir < 0 || dir >= c->desc.dims) return fail(c, FP_ERR_ARG, "fp_get_face_metrics: bad argument");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "fp_get_face_metrics");
+  const long long n = 3 * c->nface[dir];
+  if (c->is_f32) {
+    std::vector<float> tmp(n);
+    e = cudaMemcpy(tmp.data(), c->fmet[dir], n * sizeof(float), cudaMemcpyDeviceToHost);
+    for (long long i = 0; i < n; ++i) host_out[i] = tmp[i];
+  } else {
+    e = cudaMemcpy(host_out, c->fmet[dir], n * sizeof(double), cudaMemcpyDeviceToHost);
+  }
+  return e == cudaSuccess ? FP_OK : cuda_fail(c, e, "fp_get_face_metrics copy");
+}
+
+int fp_get_device_status(fp_ctx *c, void *stream) {
+  if (!c) return FP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, c->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fp_get_device_status");
+  if (word & 2) return fail(c, FP_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (word & 1) return fail(c, FP_ERR_NONFINITE, "a stage produced a non-finite state");
+  return FP_OK;
+}
+
+int fp_launches_per_rhs(const fp_ctx *c) { return c ? c->desc.dims : 0; }
+int fp_launches_per_step(const fp_ctx *c) { return c ? 3 * c->desc.dims : 0; }
+
+int fp_get_tile(const fp_ctx *c, int dir, int *faces, int *lines) {
+  if (!c || dir < 0 || dir > 2 || !faces || !lines) return FP_ERR_ARG;
+  *faces = c->hblk.dir[dir].S;
+  *lines = c->hblk.dir[dir].TT;
+  return FP_OK;
+}
+
+int fp_set_tile(fp_ctx *c, int dir, int faces, int lines) {
+  if (!c) return FP_ERR_ARG;
+  if (dir < 0 || dir >= c->desc.dims) return fail(c, FP_ERR_ARG, "fp_set_tile: bad direction");
+  if (!(faces == 8 || faces == 16 || faces == 32) || faces * lines != fpk::kThreads)
+    return fail(c, FP_ERR_ARG, "fp_set_tile: faces in {8,16,32} and faces*lines == 256");
+  c->hblk.dir[dir].S = faces;
+  c->hblk.dir[dir].TT = lines;
+  return upload_items(c);
+}
+
+// ----------------------------------------------------------------- batches
+
+void fp_batch_free(fp_batch *b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(b->dblk);
+  for (int d = 0; d < 3; ++d) cudaFree(b->items[d]);
+  cudaFree(b->dt_dev);
+  delete b;
+}
+
+const char *fp_batch_last_error(const fp_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+int fp_batch_launches_per_step(const fp_batch *b) { return b ? 3 * b->dims : 0; }
+
+static int batch_items(fp_batch *b, int d, const std::vector<int> *only_blocks) {
+  std::vector<std::pair<long long, int2>> work;
+  for (size_t k = 0; k < b->hblk.size(); ++k) {
+    if (only_blocks && std::find(only_blocks->begin(), only_blocks->end(), (int)k) == only_blocks->end())
+      continue;
+    const DirDev &D = b->hblk[k].dir[d];
+    for (long long L0 = 0; L0 < D.nlines; L0 += D.TT) {
+      long long lines = std::min<long long>(D.TT, D.nlines - L0);
+      work.push_back({(long long)D.nd * lines, make_int2((int)k, (int)L0)});
+    }
+  }
+  // largest items first: the persistent grid takes them in order
+  std::stable_sort(work.begin(), work.end(),
+                   [](const std::pair<long long, int2> &x, const std::pair<long long, int2> &y) {
+                     return x.first > y.first;
+                   });
+  std::vector<int2> it(work.size());
+  for (size_t k = 0; k < work.size(); ++k) it[k] = work[k].second;
+  cudaFree(b->items[d]);
+  b->items[d] = nullptr;
+  b->nitems[d] = (int)it.size();
+  if (it.empty()) return FP_OK;
+  cudaError_t e = cudaMalloc(&b->items[d], it.size() * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMemcpy(b->items[d], it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch items: ") + cudaGetErrorString(e));
+  return FP_OK;
+}
+
+static int batch_upload(fp_batch *b, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(b->dblk, b->hblk.data(), b->hblk.size() * sizeof(BlockDev),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+  return FP_OK;
+}
+
+static int batch_pass(fp_batch *b, int d, int mode, int stage, cudaStream_t s) {
+  fpk::SweepLaunch L;
+  L.blocks = b->dblk;
+  L.items = b->items[d];
+  L.nitems = b->nitems[d];
+  L.dir = d;
+  L.mode = mode;
+  L.stage = stage;
+  L.dt = b->dt_dev;
+  L.grid = grid_for(b->per_sm, b->nsm, L.nitems);
+  cudaError_t e = launch(b->is_f32, L, b->M, b->scheme, b->charwise, b->fp, s);
+  if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
+  return FP_OK;
+}
+
+// Autotuner: for each direction and each line-length class, time every tile shape
+// on the blocks of that class and keep the fastest.
+static int batch_autotune(fp_batch *b, cudaStream_t s) {
+  static const int cand[3][2] = {{32, 8}, {16, 16}, {8, 32}};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int d = 0; d < b->dims; ++d) {
+    const int nclass = 3;
+    for (int cl = 0; cl < nclass; ++cl) {
+      std::vector<int> members;
+      for (size_t k = 0; k < b->hblk.size(); ++k) {
+        int nd = b->hblk[k].dir[d].nd;
+        int c = nd < 64 ? 0 : (nd < 96 ? 1 : 2);
+        if (c == cl) members.push_back((int)k);
+      }
+      if (members.empty()) continue;
+      float best = 1e30f;
+      int bestc = 0;
+      for (int ci = 0; ci < 3; ++ci) {
+        for (int k : members) { b->hblk[k].dir[d].S = cand[ci][0]; b->hblk[k].dir[d].TT = cand[ci][1]; }
+        int st = batch_upload(b, s);
+        if (!st) st = batch_items(b, d, &members);
+        if (st) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+        batch_pass(b, d, fpk::MODE_WRITE, 0, s);           // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) batch_pass(b, d, fpk::MODE_WRITE, 0, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bestc = ci; }
+      }
+      for (int k : members) { b->hblk[k].dir[d].S = cand[bestc][0]; b->hblk[k].dir[d].TT = cand[bestc][1]; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  return FP_OK;
+}
+
+int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int autotune,
+                    void *stream, fp_batch **out) {
+  if (!out) return FP_ERR_ARG;
+  *out = nullptr;
+  if (!blocks || !q_devs || nblocks < 1) return FP_ERR_ARG;
+  for (int k = 0; k < nblocks; ++k)
+    if (!blocks[k] || !q_devs[k]) return FP_ERR_ARG;
+  const fp_grid_desc &d0 = blocks[0]->desc;
+  for (int k = 1; k < nblocks; ++k) {
+    const fp_grid_desc &d = blocks[k]->desc;
+    if (d.dims != d0.dims || d.metric_order != d0.metric_order || d.scheme != d0.scheme ||
+        d.precision != d0.precision || d.characteristic != d0.characteristic ||
+        d.free_stream_preserving != d0.free_stream_preserving)
+      return FP_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  fp_batch *b = new fp_batch();
+  b->dims = d0.dims; b->M = d0.metric_order; b->scheme = d0.scheme;
+  b->charwise = d0.characteristic; b->fp = d0.free_stream_preserving;
+  b->is_f32 = d0.precision == FP_F32_MIXED;
+  b->per_sm = blocks[0]->per_sm;
+  b->nsm = blocks[0]->nsm;
+  for (int k = 0; k < nblocks; ++k) {
+    b->ctx.push_back(blocks[k]);
+    BlockDev B = blocks[k]->hblk;
+    B.q[0] = q_devs[k];
+    B.dqdt = nullptr;
+    b->hblk.push_back(B);
+  }
+  cudaError_t e = cudaMalloc(&b->dblk, nblocks * sizeof(BlockDev));
+  if (e == cudaSuccess) e = cudaMalloc(&b->dt_dev, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->dt_dev, 0, sizeof(double), s);
+  if (e != cudaSuccess) { fp_batch_free(b); return FP_ERR_OOM; }
+  int st = FP_OK;
+  if (autotune) st = batch_autotune(b, s);
+  if (!st) st = batch_upload(b, s);
+  for (int d = 0; d < b->dims && !st; ++d) st = batch_items(b, d, nullptr);
+  if (st) { std::fprintf(stderr, "fp_batch_create: %s\n", b->err.c_str()); fp_batch_free(b); return st; }
+  // capture the three RK stages x directions into one graph
+  cudaStream_t cs;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { fp_batch_free(b); return FP_ERR_CUDA; }
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int stage = 0; stage < 3 && !st; ++stage)
+      for (int d = 0; d < b->dims && !st; ++d) {
+        int mode = d == 0 ? fpk::MODE_WRITE : (d == b->dims - 1 ? fpk::MODE_RK : fpk::MODE_ADD);
+        st = batch_pass(b, d, mode, stage, cs);
+      }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess && !st) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess || st) {
+    std::fprintf(stderr, "fp_batch_create: graph: %s %s\n", cudaGetErrorString(e), b->err.c_str());
+    fp_batch_free(b);
+    return st ? st : FP_ERR_CUDA;
+  }
+  *out = b;
+  return FP_OK;
+}
+
+int fp_batch_rk3_step(fp_batch *b, double dt, void *stream) {
+  if (!b) return FP_ERR_ARG;
+  if (!std::isfinite(dt)) return bfail(b, FP_ERR_ARG, "dt not finite");
+  cudaStream_t s = (cudaStream_t)stream;
+  b->dt_host = dt;
+  cudaError_t e = cudaMemcpyAsync(b->dt_dev, &b->dt_host, sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+  if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
+  return FP_OK;
+}
+
+int fp_batch_rhs(fp_batch *b, void *const *dqdt_devs, void *stream) {
+  if (!b) return FP_ERR_ARG;
+  if (!dqdt_devs) return bfail(b, FP_ERR_ARG, "null outputs");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (size_t k = 0; k < b->hblk.size(); ++k) {
+    if (!dqdt_devs[k]) return bfail(b, FP_ERR_ARG, "null output");
+    b->hblk[k].dqdt = dqdt_devs[k];
+  }
+  int st = batch_upload(b, s);
+  for (int d = 0; d < b->dims && !st; ++d) {
+    int mode = d == 0 ? fpk::MODE_WRITE : (d == b->dims - 1 ? fpk::MODE_RHS : fpk::MODE_ADD);
+    st = batch_pass(b, d, mode, 0, s);
+  }
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// fp_internal.h - device-side descriptors shared by the kernels and the C ABI of
+// libfpgb300.so.  Not part of the public interface (include/fp.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fpk {
+
+constexpr int kThreads = 256;        // threads per sweep CTA (faces per chunk x lines per tile)
+constexpr int kCellFields = 18;      // per-cell values staged in shared memory
+constexpr int kFaceFields = 5;       // per-face flux values staged in shared memory
+constexpr int kRingCells = 2 * kThreads;  // ring slots x lines per CTA (2*S*TT)
+
+// Shared-memory field indices of a staged cell.
+enum : int {
+  CF_Q = 0,      // 0..4 conserved variables
+  CF_K = 5,      // 5..7 metric vector of the swept direction (d_x, d_y, d_z)/J
+  CF_INVJ = 8,   // 1/J
+  CF_RINV = 9,   // 1/rho
+  CF_U = 10,     // 10..12 velocity
+  CF_P = 13,     // pressure
+  CF_H = 14,     // total enthalpy
+  CF_SQR = 15,   // sqrt(rho)
+  CF_UC = 16,    // contravariant velocity u . grad(d), grad(d) = J k
+  CF_AC = 17     // c |grad(d)|
+};
+
+enum : int { MODE_WRITE = 0, MODE_ADD = 1, MODE_RHS = 2, MODE_RK = 3 };
+
+// One swept direction of one block.  A "line" runs along the swept direction; the
+// lines of a block are numbered by a flattened transverse index L = t1 + nt1 * t2.
+struct DirDev {
+  int nd;              // points along the line
+  int nt1;             // extent of the first transverse coordinate
+  long long nlines;    // number of lines
+  long long qT1, qT2, qsd;  // state offsets: t1, t2 and along-line strides
+  long long mT1, mT2, msd;  // metric offsets (ghosted arrays)
+  long long fT1, fT2, fsd;  // face-metric offsets, face f+1/2 at (f+1)*fsd
+  long long fc;        // face-metric component stride
+  int bclo, bchi;      // boundary codes at the two line ends
+  int S, TT;           // faces per chunk, lines per tile (S * TT == kThreads)
+  const void *fmet;    // T [3][faces]
+};
+
+struct BlockDev {
+  DirDev dir[3];
+  int dims;
+  int G;               // metric ghost width
+  long long qc;        // state component stride (ni*nj*nk)
+  long long mc;        // metric component stride
+  long long moff;      // offset of point (0,0,0) in the metric arrays
+  const void *met;     // T [10][...] cell metrics with G ghosts
+  void *q[3];          // stage states: 0 = Q^n (caller), 1 = Q^(1), 2 = Q^(2)
+  void *racc;          // residual accumulator, state layout
+  void *dqdt;          // output of the rhs mode
+  double qbar[5];      // reference state (far-field state)
+  double gamma;
+  int *status;         // device status word: bit0 non-finite state
+};
+
+struct SweepLaunch {
+  const BlockDev *blocks;
+  const int2 *items;   // (block index, first line) per work item
+  int nitems;
+  int dir;
+  int mode;
+  int stage;           // RK stage 0,1,2 (input q[stage], output q[(stage+1)%3])
+  const double *dt;    // device scalar
+  int grid;            // CTAs of the persistent launch
+};
+
+// Launchers (sweep_f32.cu / sweep_f64.cu).  Return cudaError_t of the launch.
+cudaError_t launch_sweep_f64(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
+                             cudaStream_t s);
+cudaError_t launch_sweep_f32(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
+                             cudaStream_t s);
+// Opt in to the sweep's dynamic shared memory (all variants of one precision) and
+// return the resident CTAs per SM of the given variant.
+int prepare_sweep_f64(int M, int scheme);
+int prepare_sweep_f32(int M, int scheme);
+
+// Metric construction (metrics.cu), FP64.
+struct MetricJob {
+  int dims, M, G, Gn;
+  int n[3];
+  const double *nodes;     // device, [dims][..] with Gn ghosts
+  double *met;             // device, [10][B3]
+  double *fmet[3];         // device, face metrics per direction [3][faces]
+  double *scratch;         // device, 9 * |B2| doubles
+};
+cudaError_t build_metrics(const MetricJob &J, cudaStream_t s);
+cudaError_t convert_f64_to_f32(const double *src, float *dst, long long n, cudaStream_t s);
+
+// CFL reduction (cfl.cu).
+cudaError_t launch_cfl(const BlockDev *blk, int is_f32, long long ncells, const int *n, int dims,
+                       unsigned long long *out_bits, cudaStream_t s);
+
+}  // namespace fpk

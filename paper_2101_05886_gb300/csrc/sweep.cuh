@@ -1,0 +1,493 @@
+// sweep.cuh - the directional residual sweep of the free-stream-preserving (FP)
+// upwind finite-difference scheme (arXiv 2101.05886, Sec. 3.2), templated on the
+// arithmetic type.
+//
+// One CTA owns a tile of TT lines along the swept direction and marches along
+// them in chunks of S faces (S * TT = 256 threads, one face per thread).  Cells
+// enter a shared-memory ring (2S slots per line) once and are reused by every
+// face whose stencil covers them; per-cell primitives and spectral radii are
+// formed once per cell.  Face fluxes go to a second ring, and each cell's
+// residual contribution F'_{i+1/2} - F'_{i-1/2} (Eq. aderivative) is applied in
+// the epilogue: written, accumulated, scaled into dQ/dt, or fused into the
+// Runge-Kutta stage update.  Work items (block, line tile) are taken by a
+// persistent grid, so one launch covers every block of a batch.
+//
+// Face flux in difference form (Eq. my_point1 with the split of Eq.
+// flux_split_detail): with Q* = Q~_{i+1/2}/(1/J)_{i+1/2} (Eq. Q_star, order-M
+// interpolation, Remark 3) written as Q* = Q_i + delta,
+//   dF_m = (F(Q_m) - F(Q*)) . k_m,  dQ_m = (Q_m - Q*) (1/J)_m      m = i-2..i+3
+// are formed directly from the state differences (never as a difference of two
+// large fluxes), projected on the Roe left eigenvectors, split with local
+// Lax-Friedrichs speeds and reconstructed by WENO5-JS or linear upwind; the
+// reference face flux F(Q*) . k_{i+1/2} is added as (F(Q*) - F(Qbar)) . k_{i+1/2}
+// relative to the far-field state Qbar.  The omitted F(Qbar) . sum_d
+// (k_{i+1/2} - k_{i-1/2}) is F(Qbar) times the discrete surface-conservation
+// residual (Eq. SCL), zero to round-off for the symmetric conservative metrics.
+// Under a uniform free stream every difference is exactly zero in either
+// precision, so the state does not drift.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "fp_internal.h"
+
+namespace fpk {
+
+template <typename T> struct Num;
+template <> struct Num<double> {
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+  static __device__ __forceinline__ double ld(const void *p, long long i) {
+    return __ldg(static_cast<const double *>(p) + i);
+  }
+};
+template <> struct Num<float> {
+  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+  static __device__ __forceinline__ float ld(const void *p, long long i) {
+    return __ldg(static_cast<const float *>(p) + i);
+  }
+};
+
+// Weights of the order-M midpoint formula (Sec. 3, Eq. metric_discret), stencil
+// i-M/2+1 .. i+M/2 for the face i+1/2.
+template <int M> struct MidW;
+template <> struct MidW<2> { static __device__ __forceinline__ double w(int m) { return 0.5; } };
+template <> struct MidW<4> {
+  static __device__ __forceinline__ double w(int m) {
+    return (m == 0 || m == 3) ? -1.0 / 12.0 : 7.0 / 12.0;
+  }
+};
+template <> struct MidW<6> {
+  static __device__ __forceinline__ double w(int m) {
+    return (m == 0 || m == 5) ? 1.0 / 60.0 : (m == 1 || m == 4) ? -8.0 / 60.0 : 37.0 / 60.0;
+  }
+};
+template <> struct MidW<8> {
+  static __device__ __forceinline__ double w(int m) {
+    return (m == 0 || m == 7) ? -3.0 / 840.0
+         : (m == 1 || m == 6) ? 29.0 / 840.0
+         : (m == 2 || m == 5) ? -139.0 / 840.0 : 533.0 / 840.0;
+  }
+};
+
+// Fifth-order reconstruction at i+1/2 from v0..v4 = f_{i-2..i+2} (Sec. 2.2.2):
+// WENO5-JS with eps = 1e-6 and power 2, or linear upwind (optimal weights).
+template <typename T, int SCHEME>
+__device__ __forceinline__ T recon5(T v0, T v1, T v2, T v3, T v4) {
+  if (SCHEME == 1) {
+    return (T(2) * v0 - T(13) * v1 + T(47) * v2 + T(27) * v3 - T(3) * v4) * T(1.0 / 60.0);
+  }
+  const T s6 = T(1.0 / 6.0);
+  T q0 = (T(2) * v0 - T(7) * v1 + T(11) * v2) * s6;
+  T q1 = (-v1 + T(5) * v2 + T(2) * v3) * s6;
+  T q2 = (T(2) * v2 + T(5) * v3 - v4) * s6;
+  T d0 = v0 - T(2) * v1 + v2, e0 = v0 - T(4) * v1 + T(3) * v2;
+  T d1 = v1 - T(2) * v2 + v3, e1 = v1 - v3;
+  T d2 = v2 - T(2) * v3 + v4, e2 = T(3) * v2 - T(4) * v3 + v4;
+  const T c13 = T(13.0 / 12.0), eps = T(1.0e-6);
+  T b0 = c13 * d0 * d0 + T(0.25) * e0 * e0 + eps;
+  T b1 = c13 * d1 * d1 + T(0.25) * e1 * e1 + eps;
+  T b2 = c13 * d2 * d2 + T(0.25) * e2 * e2 + eps;
+  T a0 = Num<T>::div(T(0.1), b0 * b0);
+  T a1 = Num<T>::div(T(0.6), b1 * b1);
+  T a2 = Num<T>::div(T(0.3), b2 * b2);
+  return Num<T>::div(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+}
+
+// [F(B) - F(A)] . k from A's state (velocity uA, momentum mA, energy EA, pressure pA),
+// the difference d = B - A, and B's 1/rho and velocity; every term is a product
+// with a component of d, so the result carries the relative rounding of d.
+template <typename T>
+__device__ __forceinline__ void dflux(T g1, T rinvB, const T uB[3], const T uA[3], const T mA[3],
+                                      T EA, T pA, const T d[5], const T k[3], T out[5]) {
+  T du0 = (d[1] - uA[0] * d[0]) * rinvB;
+  T du1 = (d[2] - uA[1] * d[0]) * rinvB;
+  T du2 = (d[3] - uA[2] * d[0]) * rinvB;
+  T dke = T(0.5) * (d[1] * uB[0] + d[2] * uB[1] + d[3] * uB[2] + mA[0] * du0 + mA[1] * du1 +
+                    mA[2] * du2);
+  T dp = g1 * (d[4] - dke);
+  T UB = uB[0] * k[0] + uB[1] * k[1] + uB[2] * k[2];
+  T dU = du0 * k[0] + du1 * k[1] + du2 * k[2];
+  out[0] = d[1] * k[0] + d[2] * k[1] + d[3] * k[2];
+  out[1] = d[1] * UB + mA[0] * dU + dp * k[0];
+  out[2] = d[2] * UB + mA[1] * dU + dp * k[1];
+  out[3] = d[3] * UB + mA[2] * dU + dp * k[2];
+  out[4] = (d[4] + dp) * UB + (EA + pA) * dU;
+}
+
+template <typename T, int M, int SCHEME>
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 ? 2 : 1))
+fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, int nitems, int dir,
+         int mode, int stage, const double *__restrict__ dtp, int charwise, int fpform) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *sm = reinterpret_cast<T *>(smraw);
+  const int tid = threadIdx.x;
+
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 item = items[it];
+    const BlockDev *B = blocks + item.x;
+    const DirDev *D = &B->dir[dir];
+    const int S = D->S, TT = D->TT, W = 2 * S;
+    const bool slotFast = (dir == 0);
+    const int tf = slotFast ? (tid % S) : (tid / TT);
+    const int tl = slotFast ? (tid / S) : (tid % TT);
+    const int nd = D->nd;
+    const long long L = (long long)item.y + tl;
+    const bool lineOK = L < D->nlines;
+    const int t1 = lineOK ? (int)(L % D->nt1) : 0;
+    const int t2 = lineOK ? (int)(L / D->nt1) : 0;
+    const long long qbase = t1 * D->qT1 + t2 * D->qT2, qsd = D->qsd;
+    const long long mbase = B->moff + t1 * D->mT1 + t2 * D->mT2, msd = D->msd;
+    const long long fbase = t1 * D->fT1 + t2 * D->fT2, fsd = D->fsd, fcs = D->fc;
+    const long long qc = B->qc, mc = B->mc;
+    const int G = B->G, bclo = D->bclo, bchi = D->bchi;
+    const void *met = B->met;
+    const void *fmet = D->fmet;
+    const T *qin = static_cast<const T *>(B->q[stage]);
+    const T g1 = T(B->gamma - 1.0), gam = T(B->gamma);
+    T qb[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qb[v] = T(B->qbar[v]);
+
+    auto cidx = [&](int field, int x) -> int {
+      const int slot = x & (W - 1);
+      return field * kRingCells + (slotFast ? tl * W + slot : slot * TT + tl);
+    };
+    auto fidx = [&](int field, int x) -> int {
+      const int slot = x & (W - 1);
+      return (kCellFields + field) * kRingCells + (slotFast ? tl * W + slot : slot * TT + tl);
+    };
+
+    // Stage one cell (index x along the line) with its primitives and spectral radius.
+    auto load_cell = [&](int x) {
+      T Q[5], k[3], invJ;
+      if (x >= -G && x < nd + G) {
+        const long long mo = mbase + (long long)x * msd;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) k[a] = Num<T>::ld(met, (3LL * dir + a) * mc + mo);
+        invJ = Num<T>::ld(met, 9LL * mc + mo);
+        int xx = x;
+        bool far = false;
+        if (x < 0 || x >= nd) {
+          const int bc = x < 0 ? bclo : bchi;
+          if (bc == 0) { xx = x % nd; if (xx < 0) xx += nd; }
+          else if (bc == 1) far = true;
+          else xx = x < 0 ? 0 : nd - 1;
+        }
+        if (far) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Q[v] = qb[v];
+        } else {
+          const long long qo = qbase + (long long)xx * qsd;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Q[v] = qin[v * qc + qo];
+        }
+      } else {   // beyond every stencil that a face of this line uses
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Q[v] = qb[v];
+        k[0] = T(1); k[1] = T(0); k[2] = T(0);
+        invJ = T(1);
+      }
+      const T rinv = Num<T>::rcp(Q[0]);
+      const T u0 = Q[1] * rinv, u1 = Q[2] * rinv, u2 = Q[3] * rinv;
+      const T p = g1 * (Q[4] - T(0.5) * (Q[1] * u0 + Q[2] * u1 + Q[3] * u2));
+      const T Jc = Num<T>::rcp(invJ);
+      const T gx = Jc * k[0], gy = Jc * k[1], gz = Jc * k[2];
+      const T c = Num<T>::sqrt_(gam * p * rinv);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sm[cidx(CF_Q + v, x)] = Q[v];
+      sm[cidx(CF_K + 0, x)] = k[0];
+      sm[cidx(CF_K + 1, x)] = k[1];
+      sm[cidx(CF_K + 2, x)] = k[2];
+      sm[cidx(CF_INVJ, x)] = invJ;
+      sm[cidx(CF_RINV, x)] = rinv;
+      sm[cidx(CF_U + 0, x)] = u0;
+      sm[cidx(CF_U + 1, x)] = u1;
+      sm[cidx(CF_U + 2, x)] = u2;
+      sm[cidx(CF_P, x)] = p;
+      sm[cidx(CF_H, x)] = (Q[4] + p) * rinv;
+      sm[cidx(CF_SQR, x)] = Num<T>::sqrt_(Q[0]);
+      sm[cidx(CF_UC, x)] = u0 * gx + u1 * gy + u2 * gz;
+      sm[cidx(CF_AC, x)] = c * Num<T>::sqrt_(gx * gx + gy * gy + gz * gz);
+    };
+
+    // far-field reference state primitives (for the reference face flux)
+    const T qbr = Num<T>::rcp(qb[0]);
+    const T ub[3] = {qb[1] * qbr, qb[2] * qbr, qb[3] * qbr};
+    const T pb = g1 * (qb[4] - T(0.5) * (qb[1] * ub[0] + qb[2] * ub[1] + qb[3] * ub[2]));
+    const T mbq[3] = {qb[1], qb[2], qb[3]};
+
+    const int nch = (nd + 1 + S - 1) / S;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int a = ch * S - 1;                      // first face of the chunk
+      // ---- stage the cells this chunk's faces need that are not in the ring yet
+      if (lineOK) {
+        if (ch == 0) {
+          for (int j = tf; j < S + 8; j += S) load_cell(a - 4 + j);
+        } else {
+          load_cell(a + 4 + tf);
+        }
+      }
+      __syncthreads();
+      // ---- one face per thread: face ff + 1/2 between cells ff and ff+1
+      const int ff = a + tf;
+      if (lineOK && ff < nd) {
+        const int i0 = ff;
+        T Qi[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Qi[v] = sm[cidx(CF_Q + v, i0)];
+        T kf[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) kf[c] = Num<T>::ld(fmet, c * fcs + fbase + (long long)(ff + 1) * fsd);
+
+        // reference face state Q* = Q_i + delta (Eqs. Q_star, QdJ_star, 1dJ at order M)
+        T dl[5] = {T(0), T(0), T(0), T(0), T(0)};
+        if (fpform) {
+          T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
+          T wsum = T(0);
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            const int x = i0 - M / 2 + 1 + m;
+            const T w = T(MidW<M>::w(m)) * sm[cidx(CF_INVJ, x)];
+            wsum += w;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) acc[v] += w * (sm[cidx(CF_Q + v, x)] - Qi[v]);
+          }
+          const T wi = Num<T>::rcp(wsum);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) dl[v] = acc[v] * wi;
+        }
+        T Qs[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Qs[v] = Qi[v] + dl[v];
+        const T rinvs = Num<T>::rcp(Qs[0]);
+        const T us[3] = {Qs[1] * rinvs, Qs[2] * rinvs, Qs[3] * rinvs};
+        const T ps = g1 * (Qs[4] - T(0.5) * (Qs[1] * us[0] + Qs[2] * us[1] + Qs[3] * us[2]));
+        const T ms[3] = {Qs[1], Qs[2], Qs[3]};
+
+        // local Lax-Friedrichs speeds over the stencil cells i-2..i+3
+        T lm = T(0), l0 = T(0), lp = T(0);
+#pragma unroll
+        for (int s = -2; s <= 3; ++s) {
+          const T U = sm[cidx(CF_UC, i0 + s)], ac = sm[cidx(CF_AC, i0 + s)];
+          lm = fmax(lm, fabs(U - ac));
+          l0 = fmax(l0, fabs(U));
+          lp = fmax(lp, fabs(U + ac));
+        }
+        T lam[5];
+        if (charwise) {
+          lam[0] = lm; lam[1] = l0; lam[2] = l0; lam[3] = l0; lam[4] = lp;
+        } else {
+          const T lmax = fmax(lm, lp);
+          lam[0] = lam[1] = lam[2] = lam[3] = lam[4] = lmax;
+        }
+
+        // Roe average of cells i, i+1 and eigenvector basis in the face normal
+        const T rl = sm[cidx(CF_SQR, i0)], rr = sm[cidx(CF_SQR, i0 + 1)];
+        const T rs = Num<T>::rcp(rl + rr);
+        T u[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) u[c] = (rl * sm[cidx(CF_U + c, i0)] + rr * sm[cidx(CF_U + c, i0 + 1)]) * rs;
+        const T H = (rl * sm[cidx(CF_H, i0)] + rr * sm[cidx(CF_H, i0 + 1)]) * rs;
+        const T q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const T c2 = g1 * (H - T(0.5) * q2);
+        const T cs = Num<T>::sqrt_(c2);
+        const T csi = Num<T>::rcp(cs);
+        const T bb = g1 * csi * csi;
+        const T knr = Num<T>::rsqrt_(kf[0] * kf[0] + kf[1] * kf[1] + kf[2] * kf[2]);
+        const T n[3] = {kf[0] * knr, kf[1] * knr, kf[2] * knr};
+        T t1[3], t2[3];
+        if (n[2] * n[2] <= T(0.5)) {
+          const T s = Num<T>::rsqrt_(n[0] * n[0] + n[1] * n[1]);
+          t1[0] = -n[1] * s; t1[1] = n[0] * s; t1[2] = T(0);
+        } else {
+          const T s = Num<T>::rsqrt_(n[1] * n[1] + n[2] * n[2]);
+          t1[0] = T(0); t1[1] = n[2] * s; t1[2] = -n[1] * s;
+        }
+        t2[0] = n[1] * t1[2] - n[2] * t1[1];
+        t2[1] = n[2] * t1[0] - n[0] * t1[2];
+        t2[2] = n[0] * t1[1] - n[1] * t1[0];
+        const T Un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+        const T ut1 = u[0] * t1[0] + u[1] * t1[1] + u[2] * t1[2];
+        const T ut2 = u[0] * t2[0] + u[1] * t2[1] + u[2] * t2[2];
+
+        // characteristic projection l_s . d (rows of the Roe left-eigenvector matrix)
+        auto project = [&](const T d[5], T c[5]) {
+          if (!charwise) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) c[v] = d[v];
+            return;
+          }
+          const T X = bb * (T(0.5) * q2 * d[0] - (u[0] * d[1] + u[1] * d[2] + u[2] * d[3]) + d[4]);
+          const T Y = (Un * d[0] - (n[0] * d[1] + n[1] * d[2] + n[2] * d[3])) * csi;
+          c[0] = T(0.5) * (X + Y);
+          c[1] = d[0] - X;
+          c[2] = t1[0] * d[1] + t1[1] * d[2] + t1[2] * d[3] - ut1 * d[0];
+          c[3] = t2[0] * d[1] + t2[1] * d[2] + t2[2] * d[3] - ut2 * d[0];
+          c[4] = T(0.5) * (X - Y);
+        };
+
+        // split stencil values f+/- for m = i-2..i+3
+        T fpl[6][5], fmi[6][5];
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+          const int x = i0 - 2 + s;
+          T dF[5], dQ[5];
+          const T km[3] = {sm[cidx(CF_K, x)], sm[cidx(CF_K + 1, x)], sm[cidx(CF_K + 2, x)]};
+          const T ijm = sm[cidx(CF_INVJ, x)];
+          const T uB[3] = {sm[cidx(CF_U, x)], sm[cidx(CF_U + 1, x)], sm[cidx(CF_U + 2, x)]};
+          if (fpform) {
+            T d[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) d[v] = (sm[cidx(CF_Q + v, x)] - Qi[v]) - dl[v];
+            dflux<T>(g1, sm[cidx(CF_RINV, x)], uB, us, ms, Qs[4], ps, d, km, dF);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) dQ[v] = d[v] * ijm;
+          } else {
+            // plain scheme: F~_m and Q~_m themselves
+            T Qm[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) Qm[v] = sm[cidx(CF_Q + v, x)];
+            const T pm = sm[cidx(CF_P, x)];
+            const T U = uB[0] * km[0] + uB[1] * km[1] + uB[2] * km[2];
+            dF[0] = Qm[0] * U;
+            dF[1] = Qm[1] * U + pm * km[0];
+            dF[2] = Qm[2] * U + pm * km[1];
+            dF[3] = Qm[3] * U + pm * km[2];
+            dF[4] = (Qm[4] + pm) * U;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) dQ[v] = Qm[v] * ijm;
+          }
+          T cF[5], cQ[5];
+          project(dF, cF);
+          project(dQ, cQ);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            fpl[s][v] = T(0.5) * (cF[v] + lam[v] * cQ[v]);
+            fmi[s][v] = T(0.5) * (cF[v] - lam[v] * cQ[v]);
+          }
+        }
+        // reconstruct each field from both sides and back-project (R columns)
+        T h[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          h[v] = recon5<T, SCHEME>(fpl[0][v], fpl[1][v], fpl[2][v], fpl[3][v], fpl[4][v]) +
+                 recon5<T, SCHEME>(fmi[5][v], fmi[4][v], fmi[3][v], fmi[2][v], fmi[1][v]);
+        }
+        T F[5];
+        if (charwise) {
+          const T sa = h[0] + h[4], da = h[4] - h[0];
+          F[0] = sa + h[1];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) F[1 + c] = u[c] * (sa + h[1]) + cs * n[c] * da + t1[c] * h[2] + t2[c] * h[3];
+          F[4] = H * sa + cs * Un * da + T(0.5) * q2 * h[1] + ut1 * h[2] + ut2 * h[3];
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) F[v] = h[v];
+        }
+        if (fpform) {
+          // + F~*_{i+1/2} relative to the far-field state: (F(Q*) - F(Qbar)) . k_{i+1/2}
+          T d[5], Gf[5];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) d[v] = (Qi[v] - qb[v]) + dl[v];
+          dflux<T>(g1, rinvs, us, ub, mbq, qb[4], pb, d, kf, Gf);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) F[v] += Gf[v];
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sm[fidx(v, ff)] = F[v];
+      }
+      __syncthreads();
+      // ---- residual of cell x = a + tf from its two faces, then the epilogue
+      const int x = a + tf;
+      if (lineOK && x >= 0 && x < nd) {
+        const long long qo = qbase + (long long)x * qsd;
+        T R[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) R[v] = sm[fidx(v, x)] - sm[fidx(v, x - 1)];
+        T *racc = static_cast<T *>(B->racc);
+        if (mode == MODE_WRITE) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) racc[v * qc + qo] = R[v];
+        } else if (mode == MODE_ADD) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) racc[v * qc + qo] += R[v];
+        } else {
+          const T Jc = Num<T>::rcp(sm[cidx(CF_INVJ, x)]);
+          if (mode == MODE_RHS) {
+            T *out = static_cast<T *>(B->dqdt);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) out[v * qc + qo] = -Jc * (racc[v * qc + qo] + R[v]);
+          } else {
+            // SSP-RK3 stage (Gottlieb & Shu) in increment form:
+            // Q^(s+1) = Q^(s) + a_s (Q^n - Q^(s)) + b_s dt L(Q^(s))
+            const T dt = T(*dtp);
+            const T as = stage == 0 ? T(0) : (stage == 1 ? T(0.75) : T(1.0 / 3.0));
+            const T bs = stage == 0 ? T(1) : (stage == 1 ? T(0.25) : T(2.0 / 3.0));
+            const T *qn = static_cast<const T *>(B->q[0]);
+            T *qo_p = static_cast<T *>(B->q[(stage + 1) % 3]);
+            bool bad = false;
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              const T qk = sm[cidx(CF_Q + v, x)];
+              const T Lv = -Jc * (racc[v * qc + qo] + R[v]);
+              T nv = qk + bs * dt * Lv;
+              if (stage != 0) nv = qk + as * (qn[v * qc + qo] - qk) + bs * dt * Lv;
+              qo_p[v * qc + qo] = nv;
+              bad |= !isfinite(nv);
+            }
+            if (bad) atomicOr(B->status, 1);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T, int M, int SCHEME>
+cudaError_t launch_one(const SweepLaunch &L, int charwise, int fp, cudaStream_t s) {
+  const size_t smem = (size_t)(kCellFields + kFaceFields) * kRingCells * sizeof(T);
+  if (L.nitems <= 0) return cudaSuccess;
+  fp_sweep<T, M, SCHEME><<<L.grid, kThreads, smem, s>>>(L.blocks, L.items, L.nitems, L.dir, L.mode,
+                                                      L.stage, L.dt, charwise, fp);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sweep_t(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
+                           cudaStream_t s) {
+#define FPK_CASE(MM, SS) \
+  if (M == MM && scheme == SS) return launch_one<T, MM, SS>(L, charwise, fp, s);
+  FPK_CASE(2, 0) FPK_CASE(4, 0) FPK_CASE(6, 0) FPK_CASE(8, 0)
+  FPK_CASE(2, 1) FPK_CASE(4, 1) FPK_CASE(6, 1) FPK_CASE(8, 1)
+#undef FPK_CASE
+  return cudaErrorInvalidValue;
+}
+
+// Opt in to the dynamic shared memory of every variant and return the resident
+// CTAs per SM of the requested one.  Called before any launch or graph capture.
+template <typename T>
+int prepare_t(int M, int scheme) {
+  const size_t smem = (size_t)(kCellFields + kFaceFields) * kRingCells * sizeof(T);
+  int nb = 0;
+#define FPK_OCC(MM, SS)                                                                         \
+  {                                                                                             \
+    cudaFuncSetAttribute(fp_sweep<T, MM, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                         (int)smem);                                                            \
+    if (M == MM && scheme == SS)                                                                \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fp_sweep<T, MM, SS>, kThreads, smem);   \
+  }
+  FPK_OCC(2, 0) FPK_OCC(4, 0) FPK_OCC(6, 0) FPK_OCC(8, 0)
+  FPK_OCC(2, 1) FPK_OCC(4, 1) FPK_OCC(6, 1) FPK_OCC(8, 1)
+#undef FPK_OCC
+  return nb > 0 ? nb : 1;
+}
+
+}  // namespace fpk

@@ -1,0 +1,81 @@
+"""The C-ABI library loads and exports every symbol include/fp.h declares, and
+rejects invalid arguments before touching the GPU (runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2101_05886_gb300 import binding as B
+from paper_2101_05886_gb300 import build as BUILD
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    BUILD.build()
+    return B.lib()
+
+
+def test_header_and_binding_list_the_same_entry_points():
+    hdr = open(os.path.join(ROOT, "include", "fp.h")).read()
+    declared = set(re.findall(r"\b(fp_[a-z0-9_]+)\s*\(", hdr))
+    assert declared == set(B.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in B.EXPORTS:
+        assert hasattr(lib, name), name
+
+
+def test_ghost_widths(lib):
+    assert [B.fp_ghost_width(m) for m in (2, 4, 6, 8)] == [3, 3, 3, 4]
+    assert [B.fp_node_ghost_width(m) for m in (2, 4, 6, 8)] == [6, 9, 12, 16]
+
+
+def test_status_strings(lib):
+    for st in range(7):
+        assert lib.fp_status_string(st)
+
+
+@pytest.mark.parametrize("field,value", [("dims", 4), ("metric_order", 5), ("scheme", 7), ("precision", 3),
+                                         ("gamma", 0.9), ("characteristic", 2), ("free_stream_preserving", -1)])
+def test_invalid_descriptor_is_rejected_before_any_gpu_work(lib, field, value):
+    d = B.make_desc(3, (8, 8, 8), metric_order=6)
+    setattr(d, field, value)
+    nodes = np.zeros(3 * 32 ** 3)
+    ctx = ctypes.c_void_p()
+    st = lib.fp_init_grid(ctypes.byref(d), nodes.ctypes.data, 12, None, ctypes.byref(ctx))
+    assert st == B.FP_ERR_ARG and not ctx.value
+
+
+def test_other_invalid_arguments(lib):
+    d = B.make_desc(3, (8, 8, 8), metric_order=6)
+    nodes = np.zeros(3 * 32 ** 3)
+    ctx = ctypes.c_void_p()
+    # too few node ghost layers, extent below the ghost width, bad boundary code, 2-D with nk != 1
+    assert lib.fp_init_grid(ctypes.byref(d), nodes.ctypes.data, 11, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
+    d2 = B.make_desc(3, (2, 8, 8), metric_order=6)
+    assert lib.fp_init_grid(ctypes.byref(d2), nodes.ctypes.data, 12, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
+    d3 = B.make_desc(3, (8, 8, 8), metric_order=6, bc=((0, 5), (0, 0), (0, 0)))
+    assert lib.fp_init_grid(ctypes.byref(d3), nodes.ctypes.data, 12, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
+    d4 = B.make_desc(2, (8, 8, 3), metric_order=2)
+    assert lib.fp_init_grid(ctypes.byref(d4), nodes.ctypes.data, 6, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
+    d5 = B.make_desc(3, (8, 8, 8), metric_order=6, q_inf=(1.0, 0, 0, 0, -1.0))
+    assert lib.fp_init_grid(ctypes.byref(d5), nodes.ctypes.data, 12, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
+    assert lib.fp_init_grid(ctypes.byref(d), None, 12, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
+    assert lib.fp_init_grid(ctypes.byref(d), nodes.ctypes.data, 12, None, None) == B.FP_ERR_ARG
+    # null contexts and buffers
+    assert lib.fp_rhs(None, None, None, None) == B.FP_ERR_ARG
+    assert lib.fp_rk3_step(None, None, 0.1, None) == B.FP_ERR_ARG
+    out = ctypes.c_double()
+    assert lib.fp_cfl_dt(None, None, 0.5, ctypes.byref(out), None) == B.FP_ERR_ARG
+    assert lib.fp_get_metrics(None, None) == B.FP_ERR_ARG
+    assert lib.fp_get_device_status(None, None) == B.FP_ERR_ARG
+    assert lib.fp_batch_rk3_step(None, 0.1, None) == B.FP_ERR_ARG
+    bo = ctypes.c_void_p()
+    assert lib.fp_batch_create(None, 0, None, 0, None, ctypes.byref(bo)) == B.FP_ERR_ARG
+    lib.fp_free(None)
+    lib.fp_batch_free(None)

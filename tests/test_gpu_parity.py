@@ -1,0 +1,297 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  FP64 results must agree within 1e-12 relative per residual
+component; the FP32 form within 1e-5, with zero free-stream drift."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_2101_05886_gb300 import inputs as I
+from tests.helpers import oracle_subbox_dqdt, rel_err
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+from paper_2101_05886_gb300 import binding as B  # noqa: E402
+from paper_2101_05886_gb300.solver import Batch, Block  # noqa: E402
+
+F64, F32 = B.FP_F64, B.FP_F32_MIXED
+
+
+def _case(name, M):
+    Gn = O.node_ghost(M)
+    if name == "2d_config1":
+        g = I.wavy_sinsin_2d(n=33, amp=0.1, jitter=0.01, seed=1, Gn=Gn)
+        qinf = I.uniform_qinf(0.5, 30.0)
+        q = I.random_smooth_state(g, qinf, amp=0.05, seed=1)
+    elif name == "2d_vortex":
+        g = I.periodic_wavy_2d(40, L=10.0, amp=0.1, Gn=Gn)
+        qinf = I.uniform_qinf(0.5, 0.0, rho=1.0, p=1.0)
+        q = I.shu_vortex(*g.interior_xyz(), 0.0, 5.0, 5.0, eps=5.0, mach=0.5, L=10.0)
+    elif name == "2d_ragged":
+        g = I.periodic_wavy_2d(37, L=10.0, amp=0.1, Gn=Gn)
+        g.n = (37, 37, 1)
+        qinf = I.uniform_qinf(0.5, 0.0, rho=1.0, p=1.0)
+        q = I.shu_vortex(*g.interior_xyz(), 0.0, 5.0, 5.0, eps=5.0, mach=0.5, L=10.0)
+    elif name == "3d_vortex":
+        g = I.periodic_wavy_3d((27, 21, 19), L=10.0, amp=0.08, Gn=Gn)
+        qinf = I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0)
+        q = I.vortex_3d(g, mach=0.8, eps=5.0, L=10.0)
+    elif name == "3d_ogrid":
+        g = I.cylinder_ogrid((24, 18, 10), Lz=3.0, Gn=Gn)
+        qinf = I.uniform_qinf(3.0, 0.0)
+        q = I.random_smooth_state(g, qinf, amp=0.03, seed=4)
+    elif name == "3d_min":
+        G = O.ghost(M)
+        g = I.periodic_wavy_3d((G, G + 1, G + 2), L=1.0, amp=0.05, Gn=Gn)
+        qinf = I.uniform_qinf(0.6, 10.0, 5.0)
+        q = I.random_smooth_state(g, qinf, amp=0.05, seed=9)
+    else:
+        raise KeyError(name)
+    return g, qinf, q
+
+
+PARITY_CASES = [
+    ("2d_config1", 2, 0, 1, 1), ("2d_vortex", 6, 0, 1, 1), ("2d_vortex", 4, 1, 1, 1),
+    ("2d_ragged", 8, 0, 1, 1), ("3d_vortex", 6, 0, 1, 1), ("3d_vortex", 2, 1, 1, 1),
+    ("3d_vortex", 8, 0, 1, 1), ("3d_vortex", 6, 0, 0, 1), ("3d_vortex", 6, 0, 1, 0),
+    ("3d_ogrid", 6, 0, 1, 1), ("3d_ogrid", 4, 1, 1, 1), ("3d_min", 6, 0, 1, 1), ("3d_min", 8, 1, 1, 1),
+]
+
+
+@pytest.mark.parametrize("name,M", [("2d_config1", 2), ("2d_vortex", 8), ("3d_vortex", 6), ("3d_ogrid", 4)])
+def test_metrics_parity_fp64(name, M):
+    g, qinf, _ = _case(name, M)
+    blk = Block(g, metric_order=M, precision=F64, q_inf=qinf)
+    mg = blk.metrics()
+    mo = O.metrics(O.cfg_for(g, M=M, qinf=qinf), g.nodes, g.Gn)
+    for t in range(10):
+        scale = np.abs(mo[t]).max() or 1.0
+        assert np.abs(mg[t] - mo[t]).max() <= 1e-13 * max(scale, np.abs(mo[:9]).max()), t
+    blk.close()
+
+
+@pytest.mark.parametrize("M", [2, 6, 8])
+def test_face_metrics_are_order_M_midpoint_values(M):
+    g, qinf, _ = _case("3d_vortex", M)
+    blk = Block(g, metric_order=M, precision=F64, q_inf=qinf)
+    mo = O.metrics(O.cfg_for(g, M=M, qinf=qinf), g.nodes, g.Gn)
+    G = O.ghost(M)
+    c = O.interp_coef(M)
+    ni, nj, nk = g.n
+    for d in range(3):
+        fm = blk.face_metrics(d)
+        ax = 3 - 1 - d     # array axis of direction d in [comp][k][j][i]
+        for a in range(3):
+            arr = mo[3 * d + a]
+            # faces f+1/2, f = -1..n-1 along d: weights over cells f-M/2+1 .. f+M/2
+            nd = g.n[d]
+            ref = 0.0
+            for m in range(M):
+                idx = np.arange(-1, nd) - M // 2 + 1 + m + G
+                ref = ref + c[m] * np.take(arr, idx, axis=ax)
+            sl = [slice(G, G + nk), slice(G, G + nj), slice(G, G + ni)]
+            sl[ax] = slice(None)
+            ref = ref[tuple(sl)]
+            assert np.abs(fm[a] - ref).max() <= 1e-13 * np.abs(mo[:9]).max()
+    blk.close()
+
+
+@pytest.mark.parametrize("name,M,scheme,charwise,fp", PARITY_CASES)
+def test_rhs_parity_fp64(name, M, scheme, charwise, fp):
+    g, qinf, q = _case(name, M)
+    blk = Block(g, metric_order=M, scheme=scheme, fp=fp, characteristic=charwise, precision=F64, q_inf=qinf)
+    dq = blk.rhs(blk.to_device(q)).cpu().numpy()
+    cfg = O.cfg_for(g, M=M, scheme=scheme, fp=fp, charwise=charwise, qinf=qinf)
+    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q)
+    assert rel_err(dq, dqo) <= 1e-12
+    blk.close()
+
+
+@pytest.mark.parametrize("name,M,scheme", [("2d_vortex", 6, 0), ("3d_vortex", 6, 0), ("3d_ogrid", 6, 1)])
+def test_rk3_step_parity_fp64(name, M, scheme):
+    g, qinf, q = _case(name, M)
+    blk = Block(g, metric_order=M, scheme=scheme, precision=F64, q_inf=qinf)
+    cfg = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf)
+    met = O.metrics(cfg, g.nodes, g.Gn)
+    dt = 0.5 * O.cfl_dt(cfg, met, q, 0.5)
+    qd = blk.to_device(q)
+    qo = q.copy()
+    for _ in range(3):
+        blk.rk3_step(qd, dt)
+        qo = O.rk3_step(cfg, met, qo, dt)
+    # compare the change over the steps, scaled by its size
+    assert rel_err(qd.cpu().numpy() - q, qo - q) <= 1e-11
+    assert blk.status() == B.FP_OK
+    blk.close()
+
+
+def test_cfl_dt_parity():
+    g, qinf, q = _case("3d_vortex", 6)
+    blk = Block(g, metric_order=6, precision=F64, q_inf=qinf)
+    cfg = O.cfg_for(g, M=6, qinf=qinf)
+    dto = O.cfl_dt(cfg, O.metrics(cfg, g.nodes, g.Gn), q, 0.5)
+    assert abs(blk.cfl_dt(blk.to_device(q), 0.5) - dto) <= 1e-13 * dto
+    blk.close()
+
+
+@pytest.mark.parametrize("name,M,scheme", [("2d_vortex", 6, 0), ("3d_vortex", 6, 0), ("3d_vortex", 2, 1),
+                                           ("3d_ogrid", 6, 0)])
+def test_rhs_parity_fp32_mixed(name, M, scheme):
+    g, qinf, q = _case(name, M)
+    q32 = q.astype(np.float32).astype(np.float64)     # the same (float-representable) input on both sides
+    blk = Block(g, metric_order=M, scheme=scheme, precision=F32, q_inf=qinf)
+    dq = blk.rhs(blk.to_device(q32)).cpu().numpy()
+    cfg = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf)
+    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q32)
+    assert rel_err(dq, dqo) <= 1e-5
+    blk.close()
+
+
+def test_mach3_small_perturbation_fp32_error_scales_with_the_perturbation():
+    """FP32 error is relative to the departure from the far-field state (the FP32
+    form subtracts the reference state), not to the full flux."""
+    M = 6
+    Gn = O.node_ghost(M)
+    g = I.cylinder_ogrid((24, 18, 10), Lz=3.0, Gn=Gn)
+    qinf = I.uniform_qinf(3.0, 0.0)
+    q = I.perturbed_state(g, qinf, amp=1e-3, seed=2)
+    q32 = q.astype(np.float32).astype(np.float64)
+    blk = Block(g, metric_order=M, precision=F32, q_inf=qinf)
+    dq = blk.rhs(blk.to_device(q32)).cpu().numpy()
+    cfg = O.cfg_for(g, M=M, qinf=qinf)
+    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q32)
+    assert rel_err(dq, dqo) <= 1e-5
+    blk.close()
+
+
+@pytest.mark.parametrize("precision,M", [(F64, 2), (F64, 6), (F32, 2), (F32, 6), (F32, 8)])
+def test_config1_free_stream_ten_steps(precision, M):
+    Gn = O.node_ghost(M)
+    g = I.wavy_sinsin_2d(n=33, amp=0.1, jitter=0.01, seed=1, Gn=Gn)
+    qinf = I.uniform_qinf(0.5, 30.0)
+    blk = Block(g, metric_order=M, precision=precision, q_inf=qinf)
+    q0 = I.uniform_state(g, qinf)
+    qd = blk.to_device(q0)
+    ref = qd.clone()
+    dt = blk.cfl_dt(qd, 0.5)
+    for _ in range(10):
+        blk.rk3_step(qd, dt)
+    torch.cuda.synchronize()
+    drift = (qd - ref).abs().max().item() / np.abs(qinf).max()
+    if precision == F32:
+        assert drift == 0.0          # every difference in the FP32 form is exactly zero
+    else:
+        assert drift < 1e-13
+    blk.close()
+
+
+def test_3d_free_stream_fp32_exact_on_curvilinear_grid():
+    M = 6
+    Gn = O.node_ghost(M)
+    g = I.cylinder_ogrid((40, 33, 12), Lz=3.0, Gn=Gn)
+    qinf = I.uniform_qinf(3.0, 0.0)
+    blk = Block(g, metric_order=M, precision=F32, q_inf=qinf)
+    qd = blk.to_device(I.uniform_state(g, qinf))
+    assert blk.rhs(qd).abs().max().item() == 0.0
+    blk.close()
+
+
+def test_fp_vs_plain_on_gpu_free_stream():
+    M = 6
+    Gn = O.node_ghost(M)
+    g = I.periodic_wavy_3d((20, 18, 16), amp=0.08, Gn=Gn)
+    qinf = I.uniform_qinf(0.8, 20.0, 10.0)
+    out = {}
+    for fp in (1, 0):
+        blk = Block(g, metric_order=M, fp=fp, precision=F64, q_inf=qinf)
+        out[fp] = blk.rhs(blk.to_device(I.uniform_state(g, qinf))).abs().max().item()
+        blk.close()
+    assert out[1] < 1e-10 and out[0] > 1e-3
+
+
+def _mini_batch(precision, M=6):
+    Gn = O.node_ghost(M)
+    grids = [I.periodic_wavy_3d((33, 17, 20), amp=0.08, Gn=Gn), I.cylinder_ogrid((24, 19, 9), Lz=2.0, Gn=Gn),
+             I.periodic_wavy_3d((16, 40, 12), amp=0.08, Gn=Gn), I.cylinder_ogrid((45, 12, 14), Lz=5.0, Gn=Gn)]
+    qinf = I.uniform_qinf(3.0, 0.0)
+    blocks = [Block(g, metric_order=M, precision=precision, q_inf=qinf) for g in grids]
+    states = [b.to_device(I.random_smooth_state(g, qinf, amp=0.03, seed=k)) for k, (b, g) in enumerate(zip(blocks, grids))]
+    return grids, qinf, blocks, states
+
+
+@pytest.mark.parametrize("precision", [F64, F32])
+def test_batch_matches_single_blocks_bitwise(precision):
+    grids, qinf, blocks, states = _mini_batch(precision)
+    singles = [b.rhs(q) for b, q in zip(blocks, states)]
+    batch = Batch(blocks, states, autotune=True)
+    outs = batch.rhs([torch.empty_like(q) for q in states])
+    torch.cuda.synchronize()
+    for a, b in zip(singles, outs):
+        assert torch.equal(a, b)
+    # one RK step: batch graph replay vs per-block steps on copies
+    copies = [q.clone() for q in states]
+    dt = 1e-3
+    batch.rk3_step(dt)
+    for blk, q in zip(blocks, copies):
+        blk.rk3_step(q, dt)
+    torch.cuda.synchronize()
+    for a, b in zip(states, copies):
+        assert torch.equal(a, b)
+    batch.close()
+    for b in blocks:
+        b.close()
+
+
+def test_batch_rk3_parity_with_oracle_fp64():
+    grids, qinf, blocks, states = _mini_batch(F64, M=4)
+    q0 = [s.cpu().numpy() for s in states]
+    batch = Batch(blocks, states, autotune=False)
+    dt = 2e-3
+    batch.rk3_step(dt)
+    torch.cuda.synchronize()
+    for g, s, q in zip(grids, states, q0):
+        cfg = O.cfg_for(g, M=4, qinf=qinf)
+        qo = O.rk3_step(cfg, O.metrics(cfg, g.nodes, g.Gn), q, dt)
+        assert rel_err(s.cpu().numpy() - q, qo - q) <= 1e-11
+    batch.close()
+    for b in blocks:
+        b.close()
+
+
+def test_nonfinite_state_is_reported_not_faulted():
+    g, qinf, q = _case("3d_vortex", 6)
+    blk = Block(g, metric_order=6, precision=F64, q_inf=qinf)
+    q = q.copy()
+    q[0, 3, 4, 5] = np.nan                           # injected on the host
+    qd = blk.to_device(q)
+    blk.rk3_step(qd, 1e-3)
+    assert blk.status() == B.FP_ERR_NONFINITE
+    assert blk.status() == B.FP_OK                   # the word is cleared after reading
+    blk.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(F32, 1e-5), (F64, 1e-12)])
+def test_full_size_256cubed_sampled_parity(precision, tol):
+    """The 256^3 wavy-grid vortex case at full size: GPU dQ/dt compared with the
+    oracle on interior sub-boxes."""
+    M = 6
+    g = I.periodic_wavy_3d((256, 256, 256), L=10.0, amp=0.08, Gn=O.node_ghost(M))
+    qinf = I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0)
+    q = I.vortex_3d(g, mach=0.8, eps=5.0, L=10.0)
+    if precision == F32:
+        q = q.astype(np.float32).astype(np.float64)
+    blk = Block(g, metric_order=M, precision=precision, q_inf=qinf)
+    dq = blk.rhs(blk.to_device(q))
+    for lo in ((120, 122, 7), (3, 60, 200), (240, 5, 100)):
+        lo = np.array(lo)
+        size = np.array((8, 8, 8))
+        ref = oracle_subbox_dqdt(g, q, M, lo, size, qinf=qinf)
+        got = dq[:, lo[2]:lo[2] + 8, lo[1]:lo[1] + 8, lo[0]:lo[0] + 8].cpu().numpy()
+        full_scale = dq.abs().amax(dim=(1, 2, 3)).cpu().numpy()
+        err = max(np.abs(got[c] - ref[c]).max() / full_scale[c] for c in range(5))
+        assert err <= tol, (lo, err)
+    blk.close()
