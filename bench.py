@@ -113,7 +113,7 @@ def run_gpu(args):
     Gn = B.fp_node_ghost_width(M)
     qinf = I.uniform_qinf(3.0, 0.0)
     prec = B.FP_F32_MIXED
-    sizes = I.batched_block_sizes(64, 32, 128, 4)
+    sizes = I.batched_block_sizes(64, 32, 128, 4)[:args.blocks]
     rng = np.random.default_rng(1004)
     blocks, states = [], []
     for k, n in enumerate(sizes):
@@ -140,6 +140,7 @@ def run_gpu(args):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for s in range(args.steps):
             gstart[s].record(stream)
@@ -147,6 +148,7 @@ def run_gpu(args):
             gend[s].record(stream)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         if world > 1:
             torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
@@ -227,7 +229,8 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded grids and states)",
-            "config": {"workload": WORKLOAD, "blocks": 64, "cells_per_gpu": ncells,
+            "config": {"workload": WORKLOAD if args.blocks == 64 else WORKLOAD + f" (first {args.blocks} blocks only)",
+                       "blocks": args.blocks, "cells_per_gpu": ncells,
                        "rk_stages_per_step": 3, "precision": "FP32 sweep on FP64-built metrics",
                        "parallelism": f"independent block batches per GPU x{world}",
                        "l2": "inputs larger than L2 (state %.0f MB)" % (ncells * 20 / 1e6)},
@@ -299,12 +302,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--blocks", type=int, default=64, help="blocks of the workload (64 = the full workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

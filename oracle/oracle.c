@@ -74,22 +74,36 @@ static size_t at3(const arr3 *A, int i, int j, int k) {
 }
 static double get3(const arr3 *A, const int p[3]) { return A->a[at3(A, p[0], p[1], p[2])]; }
 
-/* derivative along direction e at point p: I_M(f)_{p+1/2} - I_M(f)_{p-1/2} (Eq. metric_discret) */
+/* derivative along direction e at point p: I_M(f)_{p+1/2} - I_M(f)_{p-1/2} (Eq. metric_discret).
+   The value at p is subtracted from the stencil first (the weights sum to one, so the
+   derivative is unchanged) to keep the sums at the size of the differences. */
 static double deriv(const arr3 *F, int M, int e, const int p[3]) {
   double fp[8], fm[8];
   int q[3];
+  const double f0 = get3(F, p);
   for (int m = 0; m < M; ++m) {
     q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
     q[e] = p[e] - M / 2 + 1 + m;
-    fp[m] = get3(F, q);
+    fp[m] = get3(F, q) - f0;
     q[e] = p[e] - M / 2 + m;
-    fm[m] = get3(F, q);
+    fm[m] = get3(F, q) - f0;
   }
   return interp_face(M, fp) - interp_face(M, fm);
 }
 
+/* derivative from the M+1 values f(p + t e), t = -M/2 .. M/2 (vals[t + M/2]) */
+static double deriv_vals(int M, const double *vals) {
+  return interp_face(M, vals + 1) - interp_face(M, vals);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Metrics: symmetric conservative metrics (Eq. JBabc) and Jacobian (Eq. JB). */
+/* The discrete SCMM does not change when the coordinates are translated (the */
+/* central derivative operators commute, the coordinate invariance the SCMM is */
+/* built to keep), so every metric and Jacobian value at a point p is formed  */
+/* from coordinates measured from the node at p.  This keeps the products in  */
+/* Eqs. JBabc and JB of the size of the metric itself and the discrete SCL    */
+/* residual at the round-off of the metrics rather than of the coordinates.  */
 /* Each metric is (1/2) * sum of four signed terms (A B)_outer, where A and B  */
 /* are a coordinate or one of its first derivatives.  Table transcribed from   */
 /* Eq. JBabc: {sign, outer, coordA, derivA, coordB, derivB}, -1 = no derivative. */
@@ -166,28 +180,28 @@ int or_metrics(const or_cfg *c, const double *nodes, int Gn, double *met) {
   arr3 m9[9];
   for (int t = 0; t < 9; ++t) m9[t] = arr_new(b2lo, b2hi);
   if (D == 3) {
-    arr3 prod = arr_new(b1lo, b1hi);
-    for (int t = 0; t < 9; ++t) {
-      for (int term = 0; term < 4; ++term) {
-        const int *T = SCMM[t][term];
-        for (int k = b1lo[2]; k < b1hi[2]; ++k)
-          for (int j = b1lo[1]; j < b1hi[1]; ++j)
-            for (int i = b1lo[0]; i < b1hi[0]; ++i) {
-              int p[3] = {i, j, k};
-              double A = T[3] == NO ? get3(&xyz[T[2]], p) : get3(&d1[T[2]][T[3]], p);
-              double B = T[5] == NO ? get3(&xyz[T[4]], p) : get3(&d1[T[4]][T[5]], p);
-              prod.a[at3(&prod, i, j, k)] = A * B;
+    for (int t = 0; t < 9; ++t)
+      for (int k = b2lo[2]; k < b2hi[2]; ++k)
+        for (int j = b2lo[1]; j < b2hi[1]; ++j)
+          for (int i = b2lo[0]; i < b2hi[0]; ++i) {
+            int p[3] = {i, j, k};
+            double x0[3];
+            for (int a = 0; a < 3; ++a) x0[a] = get3(&xyz[a], p);
+            double acc = 0.0;
+            for (int term = 0; term < 4; ++term) {
+              const int *T = SCMM[t][term];
+              double vals[9];
+              for (int tt = -M / 2; tt <= M / 2; ++tt) {
+                int r[3] = {i, j, k};
+                r[T[1]] += tt;
+                double A = T[3] == NO ? get3(&xyz[T[2]], r) - x0[T[2]] : get3(&d1[T[2]][T[3]], r);
+                double B = T[5] == NO ? get3(&xyz[T[4]], r) - x0[T[4]] : get3(&d1[T[4]][T[5]], r);
+                vals[tt + M / 2] = A * B;
+              }
+              acc += (double)T[0] * deriv_vals(M, vals);
             }
-        for (int k = b2lo[2]; k < b2hi[2]; ++k)
-          for (int j = b2lo[1]; j < b2hi[1]; ++j)
-            for (int i = b2lo[0]; i < b2hi[0]; ++i) {
-              int p[3] = {i, j, k};
-              m9[t].a[at3(&m9[t], i, j, k)] += (double)T[0] * deriv(&prod, M, T[1], p);
-            }
-      }
-      for (size_t s = 0; s < box_size(b2lo, b2hi); ++s) m9[t].a[s] *= 0.5;
-    }
-    free(prod.a);
+            m9[t].a[at3(&m9[t], i, j, k)] = 0.5 * acc;
+          }
   } else {
     /* 2-D reading of Eq. JBabc with z = zeta and z_zeta = 1:
        xi_x/J = y_eta, xi_y/J = -x_eta, eta_x/J = -y_xi, eta_y/J = x_xi. */
@@ -200,25 +214,29 @@ int or_metrics(const or_cfg *c, const double *nodes, int Gn, double *met) {
         m9[4].a[s] = get3(&d1[X][XI], (int[3]){i, j, 0});
       }
   }
-  /* Jacobian, Eq. JB: 1/J = (1/D) sum_d ( sum_a x_a (d_{x_a}/J) )_d  (factor 1/2 in 2-D) */
+  /* Jacobian, Eq. JB: 1/J = (1/D) sum_d ( sum_a x_a (d_{x_a}/J) )_d  (factor 1/2 in 2-D),
+     with x measured from the node at the point */
   arr3 invJ = arr_new(b3lo, b3hi);
-  arr3 prodJ = arr_new(b2lo, b2hi);
-  for (int d = 0; d < D; ++d) {
-    for (int k = b2lo[2]; k < b2hi[2]; ++k)
-      for (int j = b2lo[1]; j < b2hi[1]; ++j)
-        for (int i = b2lo[0]; i < b2hi[0]; ++i) {
-          int p[3] = {i, j, k};
-          double s = 0.0;
-          for (int a = 0; a < D; ++a) s += get3(&xyz[a], p) * get3(&m9[3 * d + a], p);
-          prodJ.a[at3(&prodJ, i, j, k)] = s;
+  for (int k = b3lo[2]; k < b3hi[2]; ++k)
+    for (int j = b3lo[1]; j < b3hi[1]; ++j)
+      for (int i = b3lo[0]; i < b3hi[0]; ++i) {
+        int p[3] = {i, j, k};
+        double x0[3];
+        for (int a = 0; a < 3; ++a) x0[a] = get3(&xyz[a], p);
+        double s = 0.0;
+        for (int d = 0; d < D; ++d) {
+          double vals[9];
+          for (int tt = -M / 2; tt <= M / 2; ++tt) {
+            int r[3] = {i, j, k};
+            r[d] += tt;
+            double v = 0.0;
+            for (int a = 0; a < D; ++a) v += (get3(&xyz[a], r) - x0[a]) * get3(&m9[3 * d + a], r);
+            vals[tt + M / 2] = v;
+          }
+          s += deriv_vals(M, vals);
         }
-    for (int k = b3lo[2]; k < b3hi[2]; ++k)
-      for (int j = b3lo[1]; j < b3hi[1]; ++j)
-        for (int i = b3lo[0]; i < b3hi[0]; ++i) {
-          int p[3] = {i, j, k};
-          invJ.a[at3(&invJ, i, j, k)] += deriv(&prodJ, M, d, p);
-        }
-  }
+        invJ.a[at3(&invJ, i, j, k)] = s;
+      }
   size_t n3 = box_size(b3lo, b3hi);
   for (size_t s = 0; s < n3; ++s) invJ.a[s] = invJ.a[s] / (double)D;
   /* output: 9 metrics cropped to the ghosted cell box, then 1/J */
@@ -233,7 +251,6 @@ int or_metrics(const or_cfg *c, const double *nodes, int Gn, double *met) {
   for (int a = 0; a < 3; ++a) for (int e = 0; e < 3; ++e) free(d1[a][e].a);
   for (int t = 0; t < 9; ++t) free(m9[t].a);
   free(invJ.a);
-  free(prodJ.a);
   return 0;
 }
 

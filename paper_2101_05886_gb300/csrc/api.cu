@@ -26,6 +26,7 @@ struct fp_ctx {
   long long nface[3] = {0, 0, 0};     // faces per direction
   void *met = nullptr;                // T [10][nmet]
   void *fmet[3] = {nullptr, nullptr, nullptr};
+  void *dk[3] = {nullptr, nullptr, nullptr};
   void *q1 = nullptr, *q2 = nullptr, *racc = nullptr;
   int *status = nullptr;
   double *dt_dev = nullptr;
@@ -129,6 +130,7 @@ void fill_dirs(fp_ctx *c) {
     D.bclo = c->desc.bc[d][0];
     D.bchi = c->desc.bc[d][1];
     D.fmet = c->fmet[d];
+    D.dk = c->dk[d];
     if (d < dims) default_tile(d, D.nd, &D.S, &D.TT);
     else { D.S = 8; D.TT = 32; D.nlines = 0; }
   }
@@ -236,7 +238,7 @@ void fp_free(fp_ctx *c) {
   if (!c) return;
   cudaDeviceSynchronize();
   cudaFree(c->met);
-  for (int d = 0; d < 3; ++d) { cudaFree(c->fmet[d]); cudaFree(c->items[d]); }
+  for (int d = 0; d < 3; ++d) { cudaFree(c->fmet[d]); cudaFree(c->dk[d]); cudaFree(c->items[d]); }
   cudaFree(c->q1); cudaFree(c->q2); cudaFree(c->racc);
   cudaFree(c->status); cudaFree(c->dt_dev); cudaFree(c->cfl_bits); cudaFree(c->dblk);
   delete c;
@@ -270,9 +272,13 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
 
   cudaError_t e;
   double *nodes = nullptr, *met64 = nullptr, *scratch = nullptr, *fm64[3] = {nullptr, nullptr, nullptr};
+  double *dk64[3] = {nullptr, nullptr, nullptr};
   auto cleanup_tmp = [&]() {
     cudaFree(nodes); cudaFree(scratch);
-    if (c->is_f32) { cudaFree(met64); for (int d = 0; d < 3; ++d) cudaFree(fm64[d]); }
+    if (c->is_f32) {
+      cudaFree(met64);
+      for (int d = 0; d < 3; ++d) { cudaFree(fm64[d]); cudaFree(dk64[d]); }
+    }
   };
 #define FP_TRY(call, where)                         \
   do {                                              \
@@ -292,12 +298,14 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
   FP_TRY(cudaMemcpyAsync(nodes, xyz, (size_t)dims * nnode * sizeof(double), cudaMemcpyHostToDevice, s),
          "copy nodes");
   FP_TRY(cudaMalloc(&met64, (size_t)10 * c->nmet * sizeof(double)), "cudaMalloc(metrics)");
-  for (int d = 0; d < dims; ++d)
+  for (int d = 0; d < dims; ++d) {
     FP_TRY(cudaMalloc(&fm64[d], (size_t)3 * c->nface[d] * sizeof(double)), "cudaMalloc(face metrics)");
+    FP_TRY(cudaMalloc(&dk64[d], (size_t)3 * c->ncells * sizeof(double)), "cudaMalloc(metric differences)");
+  }
   FP_TRY(cudaMalloc(&scratch, (size_t)9 * (nb1 + nb2) * sizeof(double)), "cudaMalloc(metric scratch)");
   fpk::MetricJob J;
   J.dims = dims; J.M = M; J.G = G; J.Gn = Gn;
-  for (int d = 0; d < 3; ++d) { J.n[d] = n[d]; J.fmet[d] = fm64[d]; }
+  for (int d = 0; d < 3; ++d) { J.n[d] = n[d]; J.fmet[d] = fm64[d]; J.dk[d] = dk64[d]; }
   J.nodes = nodes; J.met = met64; J.scratch = scratch;
   FP_TRY(fpk::build_metrics(J, s), "build metrics");
   if (c->is_f32) {
@@ -306,15 +314,17 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
     for (int d = 0; d < dims; ++d) {
       FP_TRY(cudaMalloc(&c->fmet[d], (size_t)3 * c->nface[d] * sizeof(float)), "cudaMalloc(face f32)");
       FP_TRY(fpk::convert_f64_to_f32(fm64[d], (float *)c->fmet[d], 3 * c->nface[d], s), "convert face metrics");
+      FP_TRY(cudaMalloc(&c->dk[d], (size_t)3 * c->ncells * sizeof(float)), "cudaMalloc(differences f32)");
+      FP_TRY(fpk::convert_f64_to_f32(dk64[d], (float *)c->dk[d], 3 * c->ncells, s), "convert differences");
     }
   } else {
     c->met = met64;
-    for (int d = 0; d < 3; ++d) c->fmet[d] = fm64[d];
+    for (int d = 0; d < 3; ++d) { c->fmet[d] = fm64[d]; c->dk[d] = dk64[d]; }
   }
   FP_TRY(cudaStreamSynchronize(s), "metric construction");
   cleanup_tmp();
   nodes = nullptr; scratch = nullptr;
-  if (c->is_f32) { met64 = nullptr; for (int d = 0; d < 3; ++d) fm64[d] = nullptr; }
+  if (c->is_f32) { met64 = nullptr; for (int d = 0; d < 3; ++d) { fm64[d] = nullptr; dk64[d] = nullptr; } }
   const size_t sbytes = (size_t)5 * c->ncells * c->esize;
   FP_TRY(cudaMalloc(&c->q1, sbytes), "cudaMalloc(stage 1)");
   FP_TRY(cudaMalloc(&c->q2, sbytes), "cudaMalloc(stage 2)");

@@ -9,7 +9,7 @@ namespace fpk {
 
 constexpr int kThreads = 256;        // threads per sweep CTA (faces per chunk x lines per tile)
 constexpr int kCellFields = 18;      // per-cell values staged in shared memory
-constexpr int kFaceFields = 5;       // per-face flux values staged in shared memory
+constexpr int kFaceFields = 10;      // per-face values staged in shared memory (W, delta)
 constexpr int kRingCells = 2 * kThreads;  // ring slots x lines per CTA (2*S*TT)
 
 // Shared-memory field indices of a staged cell.
@@ -41,6 +41,7 @@ struct DirDev {
   int bclo, bchi;      // boundary codes at the two line ends
   int S, TT;           // faces per chunk, lines per tile (S * TT == kThreads)
   const void *fmet;    // T [3][faces]
+  const void *dk;      // T [3][cells]: k_{i+1/2} - k_{i-1/2} along this direction (FP64-formed)
 };
 
 struct BlockDev {
@@ -87,6 +88,7 @@ struct MetricJob {
   const double *nodes;     // device, [dims][..] with Gn ghosts
   double *met;             // device, [10][B3]
   double *fmet[3];         // device, face metrics per direction [3][faces]
+  double *dk[3];           // device, per-point face-metric difference per direction [3][cells]
   double *scratch;         // device, 9 * |B2| doubles
 };
 cudaError_t build_metrics(const MetricJob &J, cudaStream_t s);

@@ -13,7 +13,12 @@
 //   (d_a / J) = 1/2 [ D_f(b_e c - b c_e) + D_e(b c_f - b_f c) ]
 // with (e, f) the directions and (b, c) the coordinates that follow d and a
 // cyclically.  In 2-D the metrics are the four node derivatives and the
-// Jacobian carries the factor 1/2.
+// Jacobian carries the factor 1/2.  The discrete SCMM is unchanged by a
+// translation of the coordinates (the derivative operators commute), so each
+// value is formed from coordinates and derivative stencils measured from the
+// point itself: the sums then carry the rounding of the metric's own size and
+// the discrete SCL residual stays at the metric round-off at any grid size.
+// Finally k_{i+1/2} - k_{i-1/2} is formed per point and direction in FP64.
 #include <cuda_runtime.h>
 
 #include "fp_internal.h"
@@ -78,13 +83,16 @@ __device__ __forceinline__ void unflat(long long idx, const Box &b, int p[3]) {
   p[2] = (int)(r / ny) + b.lo[2];
 }
 
-// D along e of array A (on box Ab) at point p
+// D along e of array A (on box Ab) at point p; the value at p is subtracted from
+// the stencil first (the weights sum to zero), so the sum carries the rounding of
+// the differences, not of the values.
 __device__ __forceinline__ double dpt(const double *A, const Box &Ab, const Coef &C, int e, const int p[3]) {
   const int h = C.M / 2;
   const long long st = e == 0 ? 1 : (e == 1 ? Ab.s1 : Ab.s2);
   const long long o = Ab.at(p[0], p[1], p[2]);
+  const double a0 = A[o];
   double s = 0.0;
-  for (int t = -h; t <= h; ++t) s += C.dc[t + h] * A[o + t * st];
+  for (int t = -h; t <= h; ++t) s += C.dc[t + h] * (A[o + t * st] - a0);
   return s;
 }
 
@@ -133,15 +141,17 @@ __global__ void k_metrics(const double *nodes, Box nb, const double *d1, Box b1,
         const double *bf = d1 + (b * 3 + f) * n1, *cf = d1 + (c * 3 + f) * n1;
         const long long o1 = b1.at(p[0], p[1], p[2]);
         const long long on = nb.at(p[0], p[1], p[2]);
+        // coordinates measured from the node at p (the SCMM is translation invariant)
+        const double b0 = xb[on], c0 = xc[on];
         double sF = 0.0, sE = 0.0;
         for (int t = -h; t <= h; ++t) {
           // D_f of (b_e c - b c_e)
           long long r1 = o1 + t * sf, rn = on + t * snf;
-          sF += C.dc[t + h] * (be[r1] * xc[rn] - xb[rn] * ce[r1]);
+          sF += C.dc[t + h] * (be[r1] * (xc[rn] - c0) - (xb[rn] - b0) * ce[r1]);
           // D_e of (b c_f - b_f c)
           r1 = o1 + t * se;
           rn = on + t * sne;
-          sE += C.dc[t + h] * (xb[rn] * cf[r1] - bf[r1] * xc[rn]);
+          sE += C.dc[t + h] * ((xb[rn] - b0) * cf[r1] - bf[r1] * (xc[rn] - c0));
         }
         m9[(3 * d + a) * n2 + idx] = 0.5 * (sF + sE);
       }
@@ -168,7 +178,7 @@ __global__ void k_jacobian(const double *nodes, Box nb, const double *m9, Box b2
       for (int t = -h; t <= h; ++t) {
         double prod = 0.0;
         for (int a = 0; a < dims; ++a)
-          prod += nodes[a * nn + on + t * snd] * m9[(3 * d + a) * n2 + o2 + t * s2d];
+          prod += (nodes[a * nn + on + t * snd] - nodes[a * nn + on]) * m9[(3 * d + a) * n2 + o2 + t * s2d];
         acc += C.dc[t + h] * prod;
       }
       s += acc;
@@ -204,6 +214,27 @@ __global__ void k_face_metrics(const double *met, Box b3, Coef C, int d, int n0,
   }
 }
 
+// metric difference across a cell along d: dk[a] = k_{i+1/2} - k_{i-1/2} (interior points,
+// state layout [3][nk][nj][ni])
+__global__ void k_face_diff(const double *fm, int d, int n0, int n1, int n2, double *dk) {
+  const long long ncell = (long long)n0 * n1 * n2;
+  int nf[3] = {n0, n1, n2};
+  nf[d] += 1;
+  const long long nfaces = (long long)nf[0] * nf[1] * nf[2];
+  const long long sd = d == 0 ? 1 : (d == 1 ? nf[0] : (long long)nf[0] * nf[1]);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ncell;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int p[3];
+    p[0] = (int)(idx % n0);
+    long long r = idx / n0;
+    p[1] = (int)(r % n1);
+    p[2] = (int)(r / n1);
+    // face p_d + 1/2 sits at index p_d + 1 along d, face p_d - 1/2 at p_d
+    const long long fo = (long long)p[0] + (long long)nf[0] * (p[1] + (long long)nf[1] * p[2]);
+    for (int a = 0; a < 3; ++a) dk[a * ncell + idx] = fm[a * nfaces + fo + sd] - fm[a * nfaces + fo];
+  }
+}
+
 __global__ void k_f64_to_f32(const double *src, float *dst, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -233,6 +264,8 @@ cudaError_t build_metrics(const MetricJob &J, cudaStream_t s) {
   for (int d = 0; d < J.dims; ++d) {
     long long nf = (long long)J.n[0] * J.n[1] * J.n[2] / J.n[d] * (J.n[d] + 1);
     k_face_metrics<<<grid_for(nf), 256, 0, s>>>(J.met, b3, C, d, J.n[0], J.n[1], J.n[2], J.fmet[d]);
+    const long long nc = (long long)J.n[0] * J.n[1] * J.n[2];
+    k_face_diff<<<grid_for(nc), 256, 0, s>>>(J.fmet[d], d, J.n[0], J.n[1], J.n[2], J.dk[d]);
   }
   return cudaGetLastError();
 }

@@ -18,13 +18,17 @@
 //   dF_m = (F(Q_m) - F(Q*)) . k_m,  dQ_m = (Q_m - Q*) (1/J)_m      m = i-2..i+3
 // are formed directly from the state differences (never as a difference of two
 // large fluxes), projected on the Roe left eigenvectors, split with local
-// Lax-Friedrichs speeds and reconstructed by WENO5-JS or linear upwind; the
-// reference face flux F(Q*) . k_{i+1/2} is added as (F(Q*) - F(Qbar)) . k_{i+1/2}
-// relative to the far-field state Qbar.  The omitted F(Qbar) . sum_d
-// (k_{i+1/2} - k_{i-1/2}) is F(Qbar) times the discrete surface-conservation
-// residual (Eq. SCL), zero to round-off for the symmetric conservative metrics.
-// Under a uniform free stream every difference is exactly zero in either
-// precision, so the state does not drift.
+// Lax-Friedrichs speeds and reconstructed by WENO5-JS or linear upwind into W.
+// The reference face fluxes F~*_{i+-1/2} = F(Q*_{i+-1/2}) . k_{i+-1/2} enter the
+// residual of point i through the exact identity
+//   F~*_+ - F~*_- = [F(Q*_+) - F(Q*_-)] . k_+ + [F(Q*_-) - F(Qbar)] . (k_+ - k_-)
+//                   + F(Qbar) . (k_+ - k_-),
+// with Qbar the far-field state and k_+ - k_- formed in FP64 when the metrics
+// are built.  Summed over the directions the last term is F(Qbar) times the
+// discrete surface-conservation residual (Eq. SCL), zero to round-off for the
+// symmetric conservative metrics, and is not formed.  Every remaining term is a
+// product with a difference, so FP32 arithmetic keeps its relative accuracy on
+// the residual, and a uniform free stream gives exactly zero in either precision.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -391,17 +395,11 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 #pragma unroll
           for (int v = 0; v < 5; ++v) F[v] = h[v];
         }
-        if (fpform) {
-          // + F~*_{i+1/2} relative to the far-field state: (F(Q*) - F(Qbar)) . k_{i+1/2}
-          T d[5], Gf[5];
 #pragma unroll
-          for (int v = 0; v < 5; ++v) d[v] = (Qi[v] - qb[v]) + dl[v];
-          dflux<T>(g1, rinvs, us, ub, mbq, qb[4], pb, d, kf, Gf);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) F[v] += Gf[v];
+        for (int v = 0; v < 5; ++v) {
+          sm[fidx(v, ff)] = F[v];
+          sm[fidx(5 + v, ff)] = dl[v];
         }
-#pragma unroll
-        for (int v = 0; v < 5; ++v) sm[fidx(v, ff)] = F[v];
       }
       __syncthreads();
       // ---- residual of cell x = a + tf from its two faces, then the epilogue
@@ -411,6 +409,36 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         T R[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) R[v] = sm[fidx(v, x)] - sm[fidx(v, x - 1)];
+        if (fpform) {
+          // reference states of the two faces: Q*_+ = Q_x + delta_+, Q*_- = Q_{x-1} + delta_-
+          T Qp[5], Qm[5], dQ[5], dqm[5];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const T qx = sm[cidx(CF_Q + v, x)], qx1 = sm[cidx(CF_Q + v, x - 1)];
+            const T dp = sm[fidx(5 + v, x)], dm = sm[fidx(5 + v, x - 1)];
+            Qp[v] = qx + dp;
+            Qm[v] = qx1 + dm;
+            dQ[v] = (qx - qx1) + (dp - dm);
+            dqm[v] = (qx1 - qb[v]) + dm;
+          }
+          const T rA = Num<T>::rcp(Qm[0]);
+          const T uA[3] = {Qm[1] * rA, Qm[2] * rA, Qm[3] * rA};
+          const T pA = g1 * (Qm[4] - T(0.5) * (Qm[1] * uA[0] + Qm[2] * uA[1] + Qm[3] * uA[2]));
+          const T mA[3] = {Qm[1], Qm[2], Qm[3]};
+          const T rB = Num<T>::rcp(Qp[0]);
+          const T uBp[3] = {Qp[1] * rB, Qp[2] * rB, Qp[3] * rB};
+          T kp[3], dk[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            kp[c] = Num<T>::ld(fmet, c * fcs + fbase + (long long)(x + 1) * fsd);
+            dk[c] = Num<T>::ld(D->dk, c * qc + qo);
+          }
+          T t1v[5], t2v[5];
+          dflux<T>(g1, rB, uBp, uA, mA, Qm[4], pA, dQ, kp, t1v);          // [F(Q*_+) - F(Q*_-)] . k_+
+          dflux<T>(g1, rA, uA, ub, mbq, qb[4], pb, dqm, dk, t2v);         // [F(Q*_-) - F(Qbar)] . (k_+ - k_-)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) R[v] += t1v[v] + t2v[v];
+        }
         T *racc = static_cast<T *>(B->racc);
         if (mode == MODE_WRITE) {
 #pragma unroll

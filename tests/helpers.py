@@ -4,15 +4,26 @@ import numpy as np
 import oracle as O
 
 
-def rel_err(gpu, ora, floor=0.0):
-    """Per-component max |gpu - oracle| / max(max |oracle_c|, floor); returns the max over c."""
+FLOOR_FRAC = 1e-1
+
+
+def rel_err(gpu, ora, floor_frac=FLOOR_FRAC, per_component=False):
+    """Parity metric: per component c, max |gpu - oracle| / max(max |oracle_c|, tau) with
+    tau = floor_frac * max over components of max |oracle| (10 % by default).  The
+    characteristic projection mixes the components, so their round-off shares the
+    scale of the largest one; a component whose residual is below 10 % of it is a
+    cancellation remainder (rho w of a flow that is planar up to the grid's
+    waviness falls like the truncation error as the grid is refined) and is
+    judged against 10 % of the largest component instead of its own vanishing
+    scale."""
     gpu = np.asarray(gpu, dtype=np.float64)
     ora = np.asarray(ora, dtype=np.float64)
+    tau = floor_frac * np.abs(ora).max()
     errs = []
     for c in range(ora.shape[0]):
-        scale = max(np.abs(ora[c]).max(), floor)
+        scale = max(np.abs(ora[c]).max(), tau)
         errs.append(np.abs(gpu[c] - ora[c]).max() / scale if scale > 0 else np.abs(gpu[c]).max())
-    return max(errs)
+    return errs if per_component else max(errs)
 
 
 def oracle_subbox_dqdt(grid, q, M, lo, size, scheme=0, fp=1, charwise=1, gamma=1.4, qinf=None):

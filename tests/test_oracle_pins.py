@@ -208,7 +208,7 @@ def test_surface_conservation_law_holds_to_round_off(M):
                 if ax != 2 - d:
                     dd = crop(dd, ax, h)
             Ia = Ia + dd
-        assert np.abs(Ia).max() < 1e-14 * scale * 10
+        assert np.abs(Ia).max() < 3e-15 * scale
 
 
 @pytest.mark.parametrize("M", [2, 4, 6])
