@@ -33,8 +33,9 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
 
 # Algorithmic bytes per interior point per RK stage of the FP32 form:
 # state: read Q^(s) 20 + read Q^n (stages 2,3 only: 2/3 * 20) + write Q^(s+1) 20;
-# cell metrics 9 + 1/J as float 40; face metrics 3 directions x 3 floats 36.
-BYTES_PER_CELL_STAGE_F32 = 20 + 20 * 2.0 / 3.0 + 20 + 40 + 36
+# cell metrics 9 + 1/J as float 40; face metrics 3 directions x 3 floats 36; per-point
+# face-metric differences 3 directions x 3 floats 36.
+BYTES_PER_CELL_STAGE_F32 = 20 + 20 * 2.0 / 3.0 + 20 + 40 + 36 + 36
 BYTES_PER_CELL_STAGE_F64 = 2 * BYTES_PER_CELL_STAGE_F32
 
 
