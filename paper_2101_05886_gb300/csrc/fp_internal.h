@@ -10,7 +10,9 @@ namespace fpk {
 constexpr int kThreads = 256;        // threads per sweep CTA (faces per chunk x lines per tile)
 constexpr int kCellFields = 18;      // per-cell values staged in shared memory
 constexpr int kFaceFields = 10;      // per-face values staged in shared memory (W, delta)
-constexpr int kRingCells = 2 * kThreads;  // ring slots x lines per CTA (2*S*TT)
+constexpr int kNextFields = 9;       // next chunk's cell loads staged per thread (Q, k, 1/J)
+constexpr int kEpiFields = 16;       // epilogue operands staged per thread
+constexpr int kRing = 3 * kThreads;  // shared-memory stride of one staged field (2S slots x TT lines, padded)
 
 // Shared-memory field indices of a staged cell.
 enum : int {

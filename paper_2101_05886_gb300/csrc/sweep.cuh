@@ -58,6 +58,18 @@ template <> struct Num<float> {
   }
 };
 
+// Asynchronous global -> shared copies of single elements (sm_80+ cp.async).
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T *smem, const T *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Weights of the order-M midpoint formula (Sec. 3, Eq. metric_discret), stencil
 // i-M/2+1 .. i+M/2 for the face i+1/2.
 template <int M> struct MidW;
@@ -81,27 +93,31 @@ template <> struct MidW<8> {
 };
 
 // Fifth-order reconstruction at i+1/2 from v0..v4 = f_{i-2..i+2} (Sec. 2.2.2):
-// WENO5-JS with eps = 1e-6 and power 2, or linear upwind (optimal weights).
+// WENO5-JS with eps = 1e-6 and power 2, or linear upwind (optimal weights).  Written
+// in the first differences a..d of the five values: q_k - v2 and the smoothness
+// indicators are short combinations of them, and the result is v2 + sum w_k (q_k - v2).
 template <typename T, int SCHEME>
 __device__ __forceinline__ T recon5(T v0, T v1, T v2, T v3, T v4) {
+  const T a = v1 - v0, b = v2 - v1, c = v3 - v2, d = v4 - v3;
+  // 6 (q_k - v2): (5b - 2a), (b + 2c), (4c - d)
+  const T r0 = T(5) * b - T(2) * a;
+  const T r1 = b + T(2) * c;
+  const T r2 = T(4) * c - d;
   if (SCHEME == 1) {
-    return (T(2) * v0 - T(13) * v1 + T(47) * v2 + T(27) * v3 - T(3) * v4) * T(1.0 / 60.0);
+    // optimal weights (1/10, 6/10, 3/10) over 6: (2,-13,47,27,-3)/60 relative to v2
+    return v2 + (T(0.1) * r0 + T(0.6) * r1 + T(0.3) * r2) * T(1.0 / 6.0);
   }
-  const T s6 = T(1.0 / 6.0);
-  T q0 = (T(2) * v0 - T(7) * v1 + T(11) * v2) * s6;
-  T q1 = (-v1 + T(5) * v2 + T(2) * v3) * s6;
-  T q2 = (T(2) * v2 + T(5) * v3 - v4) * s6;
-  T d0 = v0 - T(2) * v1 + v2, e0 = v0 - T(4) * v1 + T(3) * v2;
-  T d1 = v1 - T(2) * v2 + v3, e1 = v1 - v3;
-  T d2 = v2 - T(2) * v3 + v4, e2 = T(3) * v2 - T(4) * v3 + v4;
   const T c13 = T(13.0 / 12.0), eps = T(1.0e-6);
-  T b0 = c13 * d0 * d0 + T(0.25) * e0 * e0 + eps;
-  T b1 = c13 * d1 * d1 + T(0.25) * e1 * e1 + eps;
-  T b2 = c13 * d2 * d2 + T(0.25) * e2 * e2 + eps;
-  T a0 = Num<T>::div(T(0.1), b0 * b0);
-  T a1 = Num<T>::div(T(0.6), b1 * b1);
-  T a2 = Num<T>::div(T(0.3), b2 * b2);
-  return Num<T>::div(a0 * q0 + a1 * q1 + a2 * q2, a0 + a1 + a2);
+  const T d0 = b - a, e0 = T(3) * b - a;
+  const T d1 = c - b, e1 = b + c;
+  const T d2 = d - c, e2 = d - T(3) * c;
+  const T b0 = c13 * d0 * d0 + T(0.25) * e0 * e0 + eps;
+  const T b1 = c13 * d1 * d1 + T(0.25) * e1 * e1 + eps;
+  const T b2 = c13 * d2 * d2 + T(0.25) * e2 * e2 + eps;
+  const T a0 = Num<T>::div(T(0.1), b0 * b0);
+  const T a1 = Num<T>::div(T(0.6), b1 * b1);
+  const T a2 = Num<T>::div(T(0.3), b2 * b2);
+  return v2 + Num<T>::div(a0 * r0 + a1 * r1 + a2 * r2, T(6) * (a0 + a1 + a2));
 }
 
 // [F(B) - F(A)] . k from A's state (velocity uA, momentum mA, energy EA, pressure pA),
@@ -130,7 +146,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 ? 2 : 1))
 fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, int nitems, int dir,
          int mode, int stage, const double *__restrict__ dtp, int charwise, int fpform) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T *sm = reinterpret_cast<T *>(smraw);
+  T *const sm = reinterpret_cast<T *>(smraw);              // cell ring: kCellFields x kRing
+  T *const fr = sm + kCellFields * kRing;                   // face ring: kFaceFields x kRing
+  T *const nsb = fr + kFaceFields * kRing;                  // next chunk's cell, per thread: 9 x 256
+  T *const epb = nsb + kNextFields * kThreads;              // epilogue operands, per thread: 16 x 256
   const int tid = threadIdx.x;
 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -138,9 +157,17 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     const BlockDev *B = blocks + item.x;
     const DirDev *D = &B->dir[dir];
     const int S = D->S, TT = D->TT, W = 2 * S;
+    // thread roles: along-line index tf and line index tl.  The xi pass puts
+    // consecutive threads along the line (coalesced, i contiguous), the other passes
+    // across lines.  Shared layout: slot-fast lines are 3S apart (conflict-free for
+    // S < 32 as well), line-fast slots are TT apart.
     const bool slotFast = (dir == 0);
     const int tf = slotFast ? (tid % S) : (tid / TT);
     const int tl = slotFast ? (tid / S) : (tid % TT);
+    const int LS = slotFast ? 3 * S : 1;
+    const int SS = slotFast ? 1 : TT;
+    const int lbase = tl * LS;
+    const int wm = W - 1;
     const int nd = D->nd;
     const long long L = (long long)item.y + tl;
     const bool lineOK = L < D->nlines;
@@ -151,31 +178,28 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     const long long fbase = t1 * D->fT1 + t2 * D->fT2, fsd = D->fsd, fcs = D->fc;
     const long long qc = B->qc, mc = B->mc;
     const int G = B->G, bclo = D->bclo, bchi = D->bchi;
-    const void *met = B->met;
-    const void *fmet = D->fmet;
-    const T *qin = static_cast<const T *>(B->q[stage]);
+    const T *__restrict__ met = static_cast<const T *>(B->met) + mbase;
+    const T *__restrict__ fmet = static_cast<const T *>(D->fmet) + fbase;
+    const T *__restrict__ qin = static_cast<const T *>(B->q[stage]);
     const T g1 = T(B->gamma - 1.0), gam = T(B->gamma);
     T qb[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qb[v] = T(B->qbar[v]);
+    // far-field reference state primitives
+    const T qbr = Num<T>::rcp(qb[0]);
+    const T ub[3] = {qb[1] * qbr, qb[2] * qbr, qb[3] * qbr};
+    const T pb = g1 * (qb[4] - T(0.5) * (qb[1] * ub[0] + qb[2] * ub[1] + qb[3] * ub[2]));
+    const T mbq[3] = {qb[1], qb[2], qb[3]};
 
-    auto cidx = [&](int field, int x) -> int {
-      const int slot = x & (W - 1);
-      return field * kRingCells + (slotFast ? tl * W + slot : slot * TT + tl);
-    };
-    auto fidx = [&](int field, int x) -> int {
-      const int slot = x & (W - 1);
-      return (kCellFields + field) * kRingCells + (slotFast ? tl * W + slot : slot * TT + tl);
-    };
+    auto off = [&](int x) -> int { return lbase + (x & wm) * SS; };
 
-    // Stage one cell (index x along the line) with its primitives and spectral radius.
-    auto load_cell = [&](int x) {
-      T Q[5], k[3], invJ;
+    // global loads of one cell (Q, metric vector, 1/J) with the boundary rule applied
+    auto fetch = [&](int x, T Q[5], T k[3], T &invJ) {
       if (x >= -G && x < nd + G) {
-        const long long mo = mbase + (long long)x * msd;
+        const long long mo = (long long)x * msd;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) k[a] = Num<T>::ld(met, (3LL * dir + a) * mc + mo);
-        invJ = Num<T>::ld(met, 9LL * mc + mo);
+        for (int a = 0; a < 3; ++a) k[a] = met[(3LL * dir + a) * mc + mo];
+        invJ = met[9LL * mc + mo];
         int xx = x;
         bool far = false;
         if (x < 0 || x >= nd) {
@@ -188,9 +212,9 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 #pragma unroll
           for (int v = 0; v < 5; ++v) Q[v] = qb[v];
         } else {
-          const long long qo = qbase + (long long)xx * qsd;
+          const T *qp = qin + qbase + (long long)xx * qsd;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) Q[v] = qin[v * qc + qo];
+          for (int v = 0; v < 5; ++v) Q[v] = __ldg(qp + v * qc);
         }
       } else {   // beyond every stencil that a face of this line uses
 #pragma unroll
@@ -198,57 +222,123 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         k[0] = T(1); k[1] = T(0); k[2] = T(0);
         invJ = T(1);
       }
+    };
+    // primitives and spectral radius of a fetched cell into the ring
+    auto stage_cell = [&](int x, const T Q[5], const T k[3], T invJ) {
       const T rinv = Num<T>::rcp(Q[0]);
       const T u0 = Q[1] * rinv, u1 = Q[2] * rinv, u2 = Q[3] * rinv;
       const T p = g1 * (Q[4] - T(0.5) * (Q[1] * u0 + Q[2] * u1 + Q[3] * u2));
       const T Jc = Num<T>::rcp(invJ);
       const T gx = Jc * k[0], gy = Jc * k[1], gz = Jc * k[2];
       const T c = Num<T>::sqrt_(gam * p * rinv);
+      T *cp = sm + off(x);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sm[cidx(CF_Q + v, x)] = Q[v];
-      sm[cidx(CF_K + 0, x)] = k[0];
-      sm[cidx(CF_K + 1, x)] = k[1];
-      sm[cidx(CF_K + 2, x)] = k[2];
-      sm[cidx(CF_INVJ, x)] = invJ;
-      sm[cidx(CF_RINV, x)] = rinv;
-      sm[cidx(CF_U + 0, x)] = u0;
-      sm[cidx(CF_U + 1, x)] = u1;
-      sm[cidx(CF_U + 2, x)] = u2;
-      sm[cidx(CF_P, x)] = p;
-      sm[cidx(CF_H, x)] = (Q[4] + p) * rinv;
-      sm[cidx(CF_SQR, x)] = Num<T>::sqrt_(Q[0]);
-      sm[cidx(CF_UC, x)] = u0 * gx + u1 * gy + u2 * gz;
-      sm[cidx(CF_AC, x)] = c * Num<T>::sqrt_(gx * gx + gy * gy + gz * gz);
+      for (int v = 0; v < 5; ++v) cp[(CF_Q + v) * kRing] = Q[v];
+      cp[(CF_K + 0) * kRing] = k[0];
+      cp[(CF_K + 1) * kRing] = k[1];
+      cp[(CF_K + 2) * kRing] = k[2];
+      cp[CF_INVJ * kRing] = invJ;
+      cp[CF_RINV * kRing] = rinv;
+      cp[(CF_U + 0) * kRing] = u0;
+      cp[(CF_U + 1) * kRing] = u1;
+      cp[(CF_U + 2) * kRing] = u2;
+      cp[CF_P * kRing] = p;
+      cp[CF_H * kRing] = (Q[4] + p) * rinv;
+      cp[CF_SQR * kRing] = Num<T>::sqrt_(Q[0]);
+      cp[CF_UC * kRing] = u0 * gx + u1 * gy + u2 * gz;
+      cp[CF_AC * kRing] = c * Num<T>::sqrt_(gx * gx + gy * gy + gz * gz);
     };
 
-    // far-field reference state primitives (for the reference face flux)
-    const T qbr = Num<T>::rcp(qb[0]);
-    const T ub[3] = {qb[1] * qbr, qb[2] * qbr, qb[3] * qbr};
-    const T pb = g1 * (qb[4] - T(0.5) * (qb[1] * ub[0] + qb[2] * ub[1] + qb[3] * ub[2]));
-    const T mbq[3] = {qb[1], qb[2], qb[3]};
-
-    const int nch = (nd + 1 + S - 1) / S;
-    for (int ch = 0; ch < nch; ++ch) {
-      const int a = ch * S - 1;                      // first face of the chunk
-      // ---- stage the cells this chunk's faces need that are not in the ring yet
-      if (lineOK) {
-        if (ch == 0) {
-          for (int j = tf; j < S + 8; j += S) load_cell(a - 4 + j);
+    // asynchronous copy of one cell's loads into this thread's staging slots
+    auto prefetch_cell = [&](int x) {
+      T *dst = nsb + tid;
+      if (x >= -G && x < nd + G) {
+        const long long mo = (long long)x * msd;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) cp_async_el(dst + (5 + a) * kThreads, met + (3LL * dir + a) * mc + mo);
+        cp_async_el(dst + 8 * kThreads, met + 9LL * mc + mo);
+        int xx = x;
+        bool far = false;
+        if (x < 0 || x >= nd) {
+          const int bc = x < 0 ? bclo : bchi;
+          if (bc == 0) { xx = x % nd; if (xx < 0) xx += nd; }
+          else if (bc == 1) far = true;
+          else xx = x < 0 ? 0 : nd - 1;
+        }
+        if (far) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) dst[v * kThreads] = qb[v];
         } else {
-          load_cell(a + 4 + tf);
+          const T *qp = qin + qbase + (long long)xx * qsd;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) cp_async_el(dst + v * kThreads, qp + v * qc);
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dst[v * kThreads] = qb[v];
+        dst[5 * kThreads] = T(1);
+        dst[6 * kThreads] = T(0);
+        dst[7 * kThreads] = T(0);
+        dst[8 * kThreads] = T(1);
+      }
+    };
+    // asynchronous copy of the epilogue operands of cell x (residual accumulator,
+    // Q^n, metric differences, face metric of x+1/2) into this thread's slots
+    auto prefetch_epilogue = [&](int x) {
+      T *dst = epb + tid;
+      const long long qo = qbase + (long long)x * qsd;
+      if (mode != MODE_WRITE) {
+        const T *ra = static_cast<const T *>(B->racc) + qo;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) cp_async_el(dst + v * kThreads, ra + v * qc);
+      }
+      if (mode == MODE_RK && stage != 0) {
+        const T *qn = static_cast<const T *>(B->q[0]) + qo;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) cp_async_el(dst + (5 + v) * kThreads, qn + v * qc);
+      }
+      if (fpform) {
+        const T *dkp = static_cast<const T *>(D->dk) + qo;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          cp_async_el(dst + (10 + c) * kThreads, dkp + c * qc);
+          cp_async_el(dst + (13 + c) * kThreads, fmet + c * fcs + (long long)(x + 1) * fsd);
         }
       }
-      __syncthreads();
+    };
+
+    const int nch = (nd + 1 + S - 1) / S;
+    // prologue: the first chunk's window [a0-4, a0+S+4), a0 = -1
+    if (lineOK) {
+      for (int j = tf; j < S + 8; j += S) {
+        T Q[5], k[3], ij;
+        fetch(-5 + j, Q, k, ij);
+        stage_cell(-5 + j, Q, k, ij);
+      }
+    }
+    __syncthreads();
+
+    for (int ch = 0; ch < nch; ++ch) {
+      const int a = ch * S - 1;                      // first face of the chunk
+      // ---- start the loads this chunk's epilogue and the next chunk need
+      const bool nextOK = lineOK && ch + 1 < nch;
+      if (lineOK && a + tf >= 0 && a + tf < nd) prefetch_epilogue(a + tf);
+      if (nextOK) prefetch_cell(a + S + 4 + tf);
+      cp_async_commit();
       // ---- one face per thread: face ff + 1/2 between cells ff and ff+1
       const int ff = a + tf;
       if (lineOK && ff < nd) {
         const int i0 = ff;
+        int o[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = off(i0 - 3 + q);
+#define CELL(field, q) sm[(field) * kRing + o[(q)]]
         T Qi[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) Qi[v] = sm[cidx(CF_Q + v, i0)];
+        for (int v = 0; v < 5; ++v) Qi[v] = CELL(CF_Q + v, 3);
         T kf[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) kf[c] = Num<T>::ld(fmet, c * fcs + fbase + (long long)(ff + 1) * fsd);
+        for (int c = 0; c < 3; ++c) kf[c] = __ldg(fmet + c * fcs + (long long)(ff + 1) * fsd);
 
         // reference face state Q* = Q_i + delta (Eqs. Q_star, QdJ_star, 1dJ at order M)
         T dl[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -257,11 +347,11 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           T wsum = T(0);
 #pragma unroll
           for (int m = 0; m < M; ++m) {
-            const int x = i0 - M / 2 + 1 + m;
-            const T w = T(MidW<M>::w(m)) * sm[cidx(CF_INVJ, x)];
+            const int q = 3 - M / 2 + 1 + m;
+            const T w = T(MidW<M>::w(m)) * CELL(CF_INVJ, q);
             wsum += w;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) acc[v] += w * (sm[cidx(CF_Q + v, x)] - Qi[v]);
+            for (int v = 0; v < 5; ++v) acc[v] += w * (CELL(CF_Q + v, q) - Qi[v]);
           }
           const T wi = Num<T>::rcp(wsum);
 #pragma unroll
@@ -278,8 +368,8 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         // local Lax-Friedrichs speeds over the stencil cells i-2..i+3
         T lm = T(0), l0 = T(0), lp = T(0);
 #pragma unroll
-        for (int s = -2; s <= 3; ++s) {
-          const T U = sm[cidx(CF_UC, i0 + s)], ac = sm[cidx(CF_AC, i0 + s)];
+        for (int q = 1; q <= 6; ++q) {
+          const T U = CELL(CF_UC, q), ac = CELL(CF_AC, q);
           lm = fmax(lm, fabs(U - ac));
           l0 = fmax(l0, fabs(U));
           lp = fmax(lp, fabs(U + ac));
@@ -293,12 +383,12 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         }
 
         // Roe average of cells i, i+1 and eigenvector basis in the face normal
-        const T rl = sm[cidx(CF_SQR, i0)], rr = sm[cidx(CF_SQR, i0 + 1)];
+        const T rl = CELL(CF_SQR, 3), rr = CELL(CF_SQR, 4);
         const T rs = Num<T>::rcp(rl + rr);
         T u[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) u[c] = (rl * sm[cidx(CF_U + c, i0)] + rr * sm[cidx(CF_U + c, i0 + 1)]) * rs;
-        const T H = (rl * sm[cidx(CF_H, i0)] + rr * sm[cidx(CF_H, i0 + 1)]) * rs;
+        for (int c = 0; c < 3; ++c) u[c] = (rl * CELL(CF_U + c, 3) + rr * CELL(CF_U + c, 4)) * rs;
+        const T H = (rl * CELL(CF_H, 3) + rr * CELL(CF_H, 4)) * rs;
         const T q2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         const T c2 = g1 * (H - T(0.5) * q2);
         const T cs = Num<T>::sqrt_(c2);
@@ -320,63 +410,67 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         const T Un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
         const T ut1 = u[0] * t1[0] + u[1] * t1[1] + u[2] * t1[2];
         const T ut2 = u[0] * t2[0] + u[1] * t2[1] + u[2] * t2[2];
+        // half the left-eigenvector rows (the 1/2 of the Lax-Friedrichs split folded in)
+        const T qbb = T(0.25) * bb, hq2 = T(0.5) * q2, qcs = T(0.25) * csi;
+        const T h1[3] = {T(0.5) * t1[0], T(0.5) * t1[1], T(0.5) * t1[2]};
+        const T h2[3] = {T(0.5) * t2[0], T(0.5) * t2[1], T(0.5) * t2[2]};
+        const T hut1 = T(0.5) * ut1, hut2 = T(0.5) * ut2;
 
-        // characteristic projection l_s . d (rows of the Roe left-eigenvector matrix)
+        // (1/2) l_s . d for the five characteristic fields
         auto project = [&](const T d[5], T c[5]) {
           if (!charwise) {
 #pragma unroll
-            for (int v = 0; v < 5; ++v) c[v] = d[v];
+            for (int v = 0; v < 5; ++v) c[v] = T(0.5) * d[v];
             return;
           }
-          const T X = bb * (T(0.5) * q2 * d[0] - (u[0] * d[1] + u[1] * d[2] + u[2] * d[3]) + d[4]);
-          const T Y = (Un * d[0] - (n[0] * d[1] + n[1] * d[2] + n[2] * d[3])) * csi;
-          c[0] = T(0.5) * (X + Y);
-          c[1] = d[0] - X;
-          c[2] = t1[0] * d[1] + t1[1] * d[2] + t1[2] * d[3] - ut1 * d[0];
-          c[3] = t2[0] * d[1] + t2[1] * d[2] + t2[2] * d[3] - ut2 * d[0];
-          c[4] = T(0.5) * (X - Y);
+          const T X4 = qbb * (hq2 * d[0] - (u[0] * d[1] + u[1] * d[2] + u[2] * d[3]) + d[4]);
+          const T Y4 = (Un * d[0] - (n[0] * d[1] + n[1] * d[2] + n[2] * d[3])) * qcs;
+          c[0] = X4 + Y4;
+          c[1] = T(0.5) * d[0] - T(2) * X4;
+          c[2] = h1[0] * d[1] + h1[1] * d[2] + h1[2] * d[3] - hut1 * d[0];
+          c[3] = h2[0] * d[1] + h2[1] * d[2] + h2[2] * d[3] - hut2 * d[0];
+          c[4] = X4 - Y4;
         };
 
         // split stencil values f+/- for m = i-2..i+3
         T fpl[6][5], fmi[6][5];
 #pragma unroll
         for (int s = 0; s < 6; ++s) {
-          const int x = i0 - 2 + s;
-          T dF[5], dQ[5];
-          const T km[3] = {sm[cidx(CF_K, x)], sm[cidx(CF_K + 1, x)], sm[cidx(CF_K + 2, x)]};
-          const T ijm = sm[cidx(CF_INVJ, x)];
-          const T uB[3] = {sm[cidx(CF_U, x)], sm[cidx(CF_U + 1, x)], sm[cidx(CF_U + 2, x)]};
+          const int q = s + 1;
+          // dF = F~ part, d = Q part before the 1/J of the point (folded into the speeds)
+          T dF[5], d[5];
+          const T km[3] = {CELL(CF_K, q), CELL(CF_K + 1, q), CELL(CF_K + 2, q)};
+          const T ijm = CELL(CF_INVJ, q);
+          const T uB[3] = {CELL(CF_U, q), CELL(CF_U + 1, q), CELL(CF_U + 2, q)};
           if (fpform) {
-            T d[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) d[v] = (sm[cidx(CF_Q + v, x)] - Qi[v]) - dl[v];
-            dflux<T>(g1, sm[cidx(CF_RINV, x)], uB, us, ms, Qs[4], ps, d, km, dF);
-#pragma unroll
-            for (int v = 0; v < 5; ++v) dQ[v] = d[v] * ijm;
+            for (int v = 0; v < 5; ++v) d[v] = (CELL(CF_Q + v, q) - Qi[v]) - dl[v];
+            dflux<T>(g1, CELL(CF_RINV, q), uB, us, ms, Qs[4], ps, d, km, dF);
           } else {
             // plain scheme: F~_m and Q~_m themselves
-            T Qm[5];
 #pragma unroll
-            for (int v = 0; v < 5; ++v) Qm[v] = sm[cidx(CF_Q + v, x)];
-            const T pm = sm[cidx(CF_P, x)];
+            for (int v = 0; v < 5; ++v) d[v] = CELL(CF_Q + v, q);
+            const T pm = CELL(CF_P, q);
             const T U = uB[0] * km[0] + uB[1] * km[1] + uB[2] * km[2];
-            dF[0] = Qm[0] * U;
-            dF[1] = Qm[1] * U + pm * km[0];
-            dF[2] = Qm[2] * U + pm * km[1];
-            dF[3] = Qm[3] * U + pm * km[2];
-            dF[4] = (Qm[4] + pm) * U;
-#pragma unroll
-            for (int v = 0; v < 5; ++v) dQ[v] = Qm[v] * ijm;
+            dF[0] = d[0] * U;
+            dF[1] = d[1] * U + pm * km[0];
+            dF[2] = d[2] * U + pm * km[1];
+            dF[3] = d[3] * U + pm * km[2];
+            dF[4] = (d[4] + pm) * U;
           }
-          T cF[5], cQ[5];
+          T cF[5], cD[5];
           project(dF, cF);
-          project(dQ, cQ);
+          project(d, cD);
+          // f+- = (1/2) l.(dF +- lambda d (1/J)_m)
+          const T mu0 = lam[0] * ijm, mu1 = lam[1] * ijm, mu4 = lam[4] * ijm;
+          const T mu[5] = {mu0, mu1, mu1, mu1, mu4};
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
-            fpl[s][v] = T(0.5) * (cF[v] + lam[v] * cQ[v]);
-            fmi[s][v] = T(0.5) * (cF[v] - lam[v] * cQ[v]);
+            fpl[s][v] = cF[v] + mu[v] * cD[v];
+            fmi[s][v] = cF[v] - mu[v] * cD[v];
           }
         }
+#undef CELL
         // reconstruct each field from both sides and back-project (R columns)
         T h[5];
 #pragma unroll
@@ -395,27 +489,30 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 #pragma unroll
           for (int v = 0; v < 5; ++v) F[v] = h[v];
         }
+        T *fp = fr + off(ff);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          sm[fidx(v, ff)] = F[v];
-          sm[fidx(5 + v, ff)] = dl[v];
+          fp[v * kRing] = F[v];
+          fp[(5 + v) * kRing] = dl[v];
         }
       }
+      cp_async_wait_all();
       __syncthreads();
       // ---- residual of cell x = a + tf from its two faces, then the epilogue
       const int x = a + tf;
       if (lineOK && x >= 0 && x < nd) {
         const long long qo = qbase + (long long)x * qsd;
+        const int ox = off(x), oxm = off(x - 1);
         T R[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) R[v] = sm[fidx(v, x)] - sm[fidx(v, x - 1)];
+        for (int v = 0; v < 5; ++v) R[v] = fr[v * kRing + ox] - fr[v * kRing + oxm];
         if (fpform) {
           // reference states of the two faces: Q*_+ = Q_x + delta_+, Q*_- = Q_{x-1} + delta_-
           T Qp[5], Qm[5], dQ[5], dqm[5];
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
-            const T qx = sm[cidx(CF_Q + v, x)], qx1 = sm[cidx(CF_Q + v, x - 1)];
-            const T dp = sm[fidx(5 + v, x)], dm = sm[fidx(5 + v, x - 1)];
+            const T qx = sm[(CF_Q + v) * kRing + ox], qx1 = sm[(CF_Q + v) * kRing + oxm];
+            const T dp = fr[(5 + v) * kRing + ox], dm = fr[(5 + v) * kRing + oxm];
             Qp[v] = qx + dp;
             Qm[v] = qx1 + dm;
             dQ[v] = (qx - qx1) + (dp - dm);
@@ -430,8 +527,8 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           T kp[3], dk[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            kp[c] = Num<T>::ld(fmet, c * fcs + fbase + (long long)(x + 1) * fsd);
-            dk[c] = Num<T>::ld(D->dk, c * qc + qo);
+            dk[c] = epb[(10 + c) * kThreads + tid];
+            kp[c] = epb[(13 + c) * kThreads + tid];
           }
           T t1v[5], t2v[5];
           dflux<T>(g1, rB, uBp, uA, mA, Qm[4], pA, dQ, kp, t1v);          // [F(Q*_+) - F(Q*_-)] . k_+
@@ -439,40 +536,48 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 #pragma unroll
           for (int v = 0; v < 5; ++v) R[v] += t1v[v] + t2v[v];
         }
-        T *racc = static_cast<T *>(B->racc);
+        T *racc = static_cast<T *>(B->racc) + qo;
+        const T *ra = epb + tid;                      // prefetched accumulator
         if (mode == MODE_WRITE) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) racc[v * qc + qo] = R[v];
+          for (int v = 0; v < 5; ++v) racc[v * qc] = R[v];
         } else if (mode == MODE_ADD) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) racc[v * qc + qo] += R[v];
+          for (int v = 0; v < 5; ++v) racc[v * qc] = ra[v * kThreads] + R[v];
         } else {
-          const T Jc = Num<T>::rcp(sm[cidx(CF_INVJ, x)]);
+          const T Jc = Num<T>::rcp(sm[CF_INVJ * kRing + ox]);
           if (mode == MODE_RHS) {
-            T *out = static_cast<T *>(B->dqdt);
+            T *out = static_cast<T *>(B->dqdt) + qo;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) out[v * qc + qo] = -Jc * (racc[v * qc + qo] + R[v]);
+            for (int v = 0; v < 5; ++v) out[v * qc] = -Jc * (ra[v * kThreads] + R[v]);
           } else {
             // SSP-RK3 stage (Gottlieb & Shu) in increment form:
             // Q^(s+1) = Q^(s) + a_s (Q^n - Q^(s)) + b_s dt L(Q^(s))
             const T dt = T(*dtp);
             const T as = stage == 0 ? T(0) : (stage == 1 ? T(0.75) : T(1.0 / 3.0));
             const T bs = stage == 0 ? T(1) : (stage == 1 ? T(0.25) : T(2.0 / 3.0));
-            const T *qn = static_cast<const T *>(B->q[0]);
-            T *qo_p = static_cast<T *>(B->q[(stage + 1) % 3]);
+            T *qo_p = static_cast<T *>(B->q[(stage + 1) % 3]) + qo;
             bool bad = false;
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-              const T qk = sm[cidx(CF_Q + v, x)];
-              const T Lv = -Jc * (racc[v * qc + qo] + R[v]);
+              const T qk = sm[(CF_Q + v) * kRing + ox];
+              const T Lv = -Jc * (ra[v * kThreads] + R[v]);
               T nv = qk + bs * dt * Lv;
-              if (stage != 0) nv = qk + as * (qn[v * qc + qo] - qk) + bs * dt * Lv;
-              qo_p[v * qc + qo] = nv;
+              if (stage != 0) nv = qk + as * (ra[(5 + v) * kThreads] - qk) + bs * dt * Lv;
+              qo_p[v * qc] = nv;
               bad |= !isfinite(nv);
             }
             if (bad) atomicOr(B->status, 1);
           }
         }
+      }
+      __syncthreads();
+      // ---- stage the next chunk's new cell from this thread's staging slots
+      if (nextOK) {
+        const T *src = nsb + tid;
+        const T Q[5] = {src[0], src[kThreads], src[2 * kThreads], src[3 * kThreads], src[4 * kThreads]};
+        const T k[3] = {src[5 * kThreads], src[6 * kThreads], src[7 * kThreads]};
+        stage_cell(a + S + 4 + tf, Q, k, src[8 * kThreads]);
       }
       __syncthreads();
     }
@@ -481,7 +586,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 
 template <typename T, int M, int SCHEME>
 cudaError_t launch_one(const SweepLaunch &L, int charwise, int fp, cudaStream_t s) {
-  const size_t smem = (size_t)(kCellFields + kFaceFields) * kRingCells * sizeof(T);
+  const size_t smem = ((size_t)(kCellFields + kFaceFields) * kRing + (size_t)(kNextFields + kEpiFields) * kThreads) * sizeof(T);
   if (L.nitems <= 0) return cudaSuccess;
   fp_sweep<T, M, SCHEME><<<L.grid, kThreads, smem, s>>>(L.blocks, L.items, L.nitems, L.dir, L.mode,
                                                       L.stage, L.dt, charwise, fp);
@@ -503,7 +608,7 @@ cudaError_t launch_sweep_t(const SweepLaunch &L, int M, int scheme, int charwise
 // CTAs per SM of the requested one.  Called before any launch or graph capture.
 template <typename T>
 int prepare_t(int M, int scheme) {
-  const size_t smem = (size_t)(kCellFields + kFaceFields) * kRingCells * sizeof(T);
+  const size_t smem = ((size_t)(kCellFields + kFaceFields) * kRing + (size_t)(kNextFields + kEpiFields) * kThreads) * sizeof(T);
   int nb = 0;
 #define FPK_OCC(MM, SS)                                                                         \
   {                                                                                             \
