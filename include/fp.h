@@ -114,6 +114,22 @@ int fp_get_face_metrics(fp_ctx *ctx, int dir, double *host_out);
    bounded-wait timeout).  Returns FP_OK, FP_ERR_NONFINITE or FP_ERR_TIMEOUT. */
 int fp_get_device_status(fp_ctx *ctx, void *stream);
 
+/* Allocation-free residual: the result of fp_rhs, for callers that cannot allocate
+   device memory where they step (a frozen memory pool, a fixed device-memory budget, a
+   loop that must not stall on an allocation).  The paper has no counterpart; this is
+   an interface of this library.  The residual accumulator the direction passes share
+   is a file-scope static device array of 8 MiB (every GPU that loads the library holds
+   it until the process exits), and the block descriptor is a static device variable:
+   the call allocates nothing and frees nothing.  Blocks needing more than 8 MiB of
+   accumulator (more than 209,715 points in FP64, 419,430 in FP32) are rejected with
+   FP_ERR_ARG and a message in fp_last_error().  The first call on a device looks up
+   the static arrays' device addresses; make that first call before any stream
+   capture.  All calls share the static arrays, which keep the last call's contents
+   (the accumulator is fully rewritten by every call, so nothing needs clearing):
+   calls that may overlap on the GPU (different streams, several host threads) race
+   and must be serialised by the caller.  q_dev, dqdt_dev and the context as in fp_rhs. */
+int fp_rhs_noalloc(fp_ctx *ctx, const void *q_dev, void *dqdt_dev, void *stream);
+
 /* Number of kernel launches one fp_rhs / fp_rk3_step call queues. */
 int fp_launches_per_rhs(const fp_ctx *ctx);
 int fp_launches_per_step(const fp_ctx *ctx);

@@ -20,7 +20,7 @@ FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP = 0, 1, 2
 
 # every symbol include/fp.h declares
 EXPORTS = [
-    "fp_ghost_width", "fp_node_ghost_width", "fp_init_grid", "fp_rhs", "fp_rk3_step", "fp_cfl_dt",
+    "fp_ghost_width", "fp_node_ghost_width", "fp_init_grid", "fp_rhs", "fp_rhs_noalloc", "fp_rk3_step", "fp_cfl_dt",
     "fp_get_metrics", "fp_get_face_metrics", "fp_get_device_status", "fp_launches_per_rhs",
     "fp_launches_per_step", "fp_get_tile", "fp_set_tile", "fp_last_error", "fp_status_string",
     "fp_free", "fp_batch_create", "fp_batch_rk3_step", "fp_batch_rhs", "fp_batch_launches_per_step",
@@ -51,6 +51,7 @@ def lib():
         L.fp_node_ghost_width.argtypes = [ctypes.c_int]
         L.fp_init_grid.argtypes = [ctypes.POINTER(fp_grid_desc), _VP, ctypes.c_int, _VP, ctypes.POINTER(_VP)]
         L.fp_rhs.argtypes = [_VP, _VP, _VP, _VP]
+        L.fp_rhs_noalloc.argtypes = [_VP, _VP, _VP, _VP]
         L.fp_rk3_step.argtypes = [_VP, _VP, ctypes.c_double, _VP]
         L.fp_cfl_dt.argtypes = [_VP, _VP, ctypes.c_double, ctypes.POINTER(ctypes.c_double), _VP]
         L.fp_get_metrics.argtypes = [_VP, _VP]
@@ -133,6 +134,11 @@ def fp_init_grid(desc, nodes_host_ptr, ghost_nodes, stream=0):
 
 def fp_rhs(ctx, q_ptr, dqdt_ptr, stream=0):
     _check(lib().fp_rhs(ctx, q_ptr, dqdt_ptr, stream), ctx)
+
+
+def fp_rhs_noalloc(ctx, q_ptr, dqdt_ptr, stream=0):
+    """fp_rhs with its residual accumulator in the library's static device scratch."""
+    _check(lib().fp_rhs_noalloc(ctx, q_ptr, dqdt_ptr, stream), ctx)
 
 
 def fp_rk3_step(ctx, q_ptr, dt, stream=0):

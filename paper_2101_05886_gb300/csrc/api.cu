@@ -680,3 +680,77 @@ int fp_batch_rhs(fp_batch *b, void *const *dqdt_devs, void *stream) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------- allocation-free residual
+//
+// fp_rhs_noalloc: the same residual as fp_rhs, for callers that must not allocate device
+// memory inside their time loop (a host framework with a frozen memory pool or a fixed
+// device-memory budget, a real-time loop where an allocation would stall, code that
+// runs while other work is being captured into a graph and so may not call cudaMalloc).
+// The residual accumulator the three direction passes share lives in a fixed static
+// device array instead of context memory, and the block descriptor it needs in a static
+// device variable; the call itself allocates nothing.
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;      // 8 MiB, held by every GPU that loads the library
+__device__ __align__(256) unsigned char g_noalloc_racc[kNoAllocScratchBytes];
+__device__ __align__(256) BlockDev g_noalloc_block;
+constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocDevice {
+  void *racc = nullptr;
+  BlockDev *blk = nullptr;
+  bool ready = false;
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+}  // namespace
+
+extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream) {
+  if (!c) return FP_ERR_ARG;
+  if (!q || !dqdt) return fail(c, FP_ERR_ARG, "fp_rhs_noalloc: null buffer");
+  const size_t need = (size_t)5 * (size_t)c->ncells * c->esize;
+  if (need > kNoAllocScratchBytes) {
+    char msg[256];
+    std::snprintf(msg, sizeof msg,
+                  "fp_rhs_noalloc: the block needs %zu bytes of residual scratch but the static "
+                  "scratch holds %zu (at most %zu points in FP64, %zu in FP32)",
+                  need, kNoAllocScratchBytes, kNoAllocScratchBytes / 40, kNoAllocScratchBytes / 20);
+    return fail(c, FP_ERR_ARG, msg);
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(c, FP_ERR_UNSUPPORTED, "fp_rhs_noalloc: device ordinal beyond 63");
+  NoAllocDevice &S = g_noalloc_dev[dev];
+  if (!S.ready) {
+    // once per device, with that device current: device addresses of the static arrays
+    e = cudaGetSymbolAddress(&S.racc, g_noalloc_racc);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: cudaGetSymbolAddress(scratch)");
+    void *bp = nullptr;
+    e = cudaGetSymbolAddress(&bp, g_noalloc_block);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: cudaGetSymbolAddress(descriptor)");
+    S.blk = static_cast<BlockDev *>(bp);
+    S.ready = true;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  BlockDev b = c->hblk;
+  b.q[0] = const_cast<void *>(q);
+  b.dqdt = dqdt;
+  b.racc = S.racc;                     // fully written by the first pass: nothing to clear
+  e = cudaMemcpyAsync(S.blk, &b, sizeof(BlockDev), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: descriptor upload");
+  const int dims = c->desc.dims, M = c->desc.metric_order;
+  for (int d = 0; d < dims; ++d) {
+    fpk::SweepLaunch L;
+    L.blocks = S.blk;
+    L.items = c->items[d];
+    L.nitems = c->nitems[d];
+    L.dir = d;
+    L.mode = d == 0 ? fpk::MODE_WRITE : (d == dims - 1 ? fpk::MODE_RHS : fpk::MODE_ADD);
+    L.stage = 0;
+    L.dt = c->dt_dev;
+    L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
+    e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic, c->desc.free_stream_preserving, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: sweep launch");
+  }
+  return FP_OK;
+}
