@@ -37,6 +37,15 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
 # face-metric differences 3 directions x 3 floats 36.
 BYTES_PER_CELL_STAGE_F32 = 20 + 20 * 2.0 / 3.0 + 20 + 40 + 36 + 36
 BYTES_PER_CELL_STAGE_F64 = 2 * BYTES_PER_CELL_STAGE_F32
+# FP32 floating-point operations per point per direction pass of the WENO5-JS FP sweep
+# (FFMA counted as 2), counted by ncu on the 16-block subset of the workload
+# (profiles/fp_sweep_f32_batched16_full.md).  The pass is bound by FP32 issue.
+FLOPS_PER_POINT_PASS_F32 = 2280.0
+# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch measured by ncu for the current kernel (16-block capture, 94.5 B per
+# point per pass), scaled to a launch over the 64-block workload.
+TRAFFIC_BYTES_PER_POINT_PASS = 94.5
 
 
 def _dist():
@@ -88,6 +97,23 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def max_over_ranks(x, device="cpu"):
+    """Max of a per-rank scalar over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(points_per_rank, stages, ms_max, world):
+    """Whole-job Mcell-RHS/s per RK stage: every rank advances its own blocks, the job
+    takes as long as the slowest rank."""
+    return world * points_per_rank * stages / (ms_max * 1e-3) / 1e6
 
 
 def peaks():
@@ -154,12 +180,9 @@ def run_gpu(args):
             torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
     graph_ms = sum(a.elapsed_time(b) for a, b in zip(gstart, gend))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ms, "cuda")
     stages = 3 * args.steps
-    value = world * ncells * stages / (ms * 1e-3) / 1e6
+    value = weak_scaling_value(ncells, stages, ms, world)
     launches_per_step = batch.launches_per_step()
     st = [b.status() for b in blocks]
     assert all(s == B.FP_OK for s in st), "non-finite state during the benchmark"
@@ -182,22 +205,26 @@ def run_gpu(args):
                 h.copy_(q, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
-        ems = f0.elapsed_time(f1)
-        if world > 1:
-            t = torch.tensor([ems], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = t.item()
-        e2e = {"value": world * ncells * stages / (ems * 1e-3) / 1e6, "unit": "Mcell/s",
+        ems = max_over_ranks(f0.elapsed_time(f1), "cuda")
+        e2e = {"value": weak_scaling_value(ncells, stages, ems, world), "unit": "Mcell/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d}
 
     # ---- roofline of the dominant kernel (the sweep; every launch in the graph is one)
     hbm, src = peaks()
     per_launch_ms = graph_ms / (args.steps * launches_per_step)
     alg_bytes_per_launch = BYTES_PER_CELL_STAGE_F32 * ncells / 3.0     # one of the 3 direction passes
-    achieved = alg_bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
-            "kernel": "fpk::fp_sweep<float,6,0>", "launch_ms": round(per_launch_ms, 4)}
+    achieved_gbs = alg_bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
+    flops_per_launch = FLOPS_PER_POINT_PASS_F32 * ncells
+    achieved_tf = flops_per_launch / (per_launch_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved_tf, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
+            "unit": "TFLOP/s", "frac": round(achieved_tf / FP32_PEAK_TFLOPS, 4),
+            "traffic": round(TRAFFIC_BYTES_PER_POINT_PASS * ncells) if args.blocks == 64 else None,
+            "peak_source": "FP32 unit count x 2.07 GHz (see DESIGN.md)",
+            "kernel": "fpk::fp_sweep<float,6,0>", "launch_ms": round(per_launch_ms, 4),
+            "algorithmic_flops_per_launch": flops_per_launch,
+            "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved_gbs / hbm, 4), "peak_source": src,
+                    "algorithmic_bytes_per_point_stage": round(BYTES_PER_CELL_STAGE_F32, 1)}}
 
     # ---- FP64 plain single block (256^3 wavy grid + vortex) on the same GPU
     fp64 = None
@@ -222,6 +249,16 @@ def run_gpu(args):
                 "ms_per_step": ms64 / n64, "dtype": "f64"}
         b64.close()
 
+    # ---- single large C-grid (512 x 384 x 512, about 100M points), FP32 and FP64 plain
+    c5 = None
+    if args.c5 and rank == 0:
+        for b in blocks:
+            b.close()
+        batch.close()
+        blocks, states = [], []
+        torch.cuda.empty_cache()
+        c5 = run_c5(args, I, B, Block, Gn, M, torch, stream)
+
     result = None
     if rank == 0:
         cpu = None if args.no_cpu else cpu_baseline(args)
@@ -237,6 +274,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (state %.0f MB)" % (ncells * 20 / 1e6)},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "fp64_plain_single_block": fp64,
+            "c5_single_large": c5,
         }
         print(json.dumps(result))
     for b in blocks:
@@ -244,6 +282,40 @@ def run_gpu(args):
     batch.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_c5(args, I, B, Block, Gn, M, torch, stream):
+    """C-grid 512x384x512 around a swept tapered wing-like body, Mach 0.84 at 3 degrees,
+    uniform initial state: FP32 sweep timed over args.c5_steps RK3 steps, FP64 plain over 1."""
+    g = I.cgrid_wing(n=(512, 384, 512), Gn=Gn)
+    qinf = I.uniform_qinf(0.84, 3.0)
+    ncell = 512 * 384 * 512
+    out = {"workload": "C-grid 512x384x512 (100.7M points), swept tapered thick wing-like body, "
+                       "tanh wall spacing 1e-4 chord, Mach 0.84 at 3 deg, uniform start, WENO5-JS FP, M6"}
+    for prec, key, nsteps in ((B.FP_F32_MIXED, "fp32", args.c5_steps), (B.FP_F64, "fp64", 1)):
+        blk = Block(g, metric_order=M, precision=prec, q_inf=qinf)
+        q = blk.to_device(I.uniform_state(g, qinf))
+        ref = q.clone() if prec == B.FP_F32_MIXED else None
+        dt = blk.cfl_dt(q, 0.5)
+        blk.rk3_step(q, dt)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(nsteps):
+            blk.rk3_step(q, dt)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out[key] = {"value": round(ncell * 3 * nsteps / (ms * 1e-3) / 1e6, 2), "unit": "Mcell/s",
+                    "ms_per_step": round(ms / nsteps, 3), "steps": nsteps}
+        if ref is not None:
+            out[key]["free_stream_drift"] = float((q - ref).abs().max().item())
+        assert blk.status() == B.FP_OK
+        blk.close()
+        del q, ref
+        torch.cuda.empty_cache()
+    del g
+    return out
 
 
 def _oracle_sample(seconds_target=10.0, n=40):
@@ -310,6 +382,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--blocks", type=int, default=64, help="blocks of the workload (64 = the full workload)")
+    ap.add_argument("--c5", type=int, default=1, help="also time the single 100M-point C-grid (1/0)")
+    ap.add_argument("--c5-steps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -223,19 +223,37 @@ def _stretch_beta(first, npts):
     return 0.5 * (lo + hi)
 
 
+def _growth_ratio(first, total, steps):
+    """r such that first * (r**steps - 1)/(r - 1) == total (bisection, r > 1)."""
+    lo, hi = 1.0 + 1e-9, 2.0
+    while first * (hi ** steps - 1.0) / (hi - 1.0) < total:
+        hi *= 1.5
+    for _ in range(200):
+        r = 0.5 * (lo + hi)
+        if first * (r ** steps - 1.0) / (r - 1.0) < total:
+            lo = r
+        else:
+            hi = r
+    return 0.5 * (lo + hi)
+
+
 def cgrid_wing(n=(512, 384, 512), tc=0.15, taper=0.5, sweep_deg=30.0, span=3.0,
                far=20.0, first_cell=1e-4, wake_frac=0.25, Gn=6, dtype=np.float64):
-    """Single-block C-grid around a swept, tapered, extruded thick-ellipse body.
+    """Single-block C-grid around a swept, tapered, extruded thick wing-like body.
 
     i wraps from the lower wake outflow, around the body (trailing edge -> leading
     edge -> trailing edge) to the upper wake outflow; j runs from the body/wake
     line to a far field `far` chords away with tanh stretching (first node offset
-    `first_cell` chords); k runs along the span.  The inner curve at span station z
-    is an ellipse of chord c(z) = 1 - (1-taper) z/span and thickness tc*c(z) whose
-    leading edge is swept back by z*tan(sweep); the wake lines run downstream from
-    the trailing edge.  Grid lines leave the inner curve along a direction that
-    turns continuously from -y (lower wake) through -x (leading edge) to +y (upper
-    wake).  Ghost nodes are the same formulas evaluated outside the index ranges.
+    `first_cell` chords); k runs along the span.  At span station z the chord is
+    c(z) = 1 - (1-taper) z/span and the leading edge is swept back by z*tan(sweep).
+    The section, with body parameter t in [-1, 1] (1 lower trailing edge, 0 leading
+    edge), is x = c t^2, y = -K c t (1 - t^2): round-nosed (y ~ sqrt(x) at the
+    leading edge, like an ellipse), thickness tc*c, and a finite trailing-edge wedge
+    so the wake lines leave it without a kink.  Wake points are spaced geometrically
+    from the body's trailing-edge spacing out to `far` chords.  Grid lines leave the
+    inner curve along a direction that turns continuously from -y (lower wake)
+    through -x (leading edge) to +y (upper wake).  Ghost nodes are the same formulas
+    evaluated outside the index ranges.
     """
     ni, nj, nk = n
     beta = _stretch_beta(first_cell / far, nj)
@@ -249,16 +267,20 @@ def cgrid_wing(n=(512, 384, 512), tc=0.15, taper=0.5, sweep_deg=30.0, span=3.0,
     xle = z * math.tan(math.radians(sweep_deg))
     wf = wake_frac
     sb = np.clip((s - wf) / (1.0 - 2 * wf), 0.0, 1.0)  # body fraction
-    phi = 2 * np.pi * sb                               # 0 lower TE, pi LE, 2pi upper TE
-    wlen = far * (np.clip((wf - s) / wf, 0.0, None) + np.clip((s - (1 - wf)) / wf, 0.0, None))
+    t = 1.0 - 2.0 * sb
+    kth = tc / (2.0 * (2.0 / 3.0) * math.sqrt(1.0 / 3.0))   # max of t(1-t^2) is (2/3)sqrt(1/3)
+    sig = np.maximum((wf - s) / wf, 0.0) + np.maximum((s - (1.0 - wf)) / wf, 0.0)  # wake fraction
+    steps = wf * (ni - 1)                              # wake intervals on each side
+    first = 4.0 / ((1.0 - 2 * wf) * (ni - 1))          # body trailing-edge step in chords
     psi = -0.5 * np.pi - np.pi * sb                    # outward direction angle
     dx, dy = np.cos(psi), np.sin(psi)
-    cx = 0.5 * (1.0 + np.cos(phi))                     # chord fraction, 1 at TE
-    cy = -0.5 * tc * np.sin(phi)
     nodes = np.empty((3, k.size, j.size, i.size), dtype=dtype)
     for kk in range(k.size):
-        xin = xle[kk] + chord[kk] * cx + wlen
-        yin = chord[kk] * cy
+        c = chord[kk]
+        r = _growth_ratio(first, far / c, steps)
+        wl = c * first * (r ** (sig * steps) - 1.0) / (r - 1.0)
+        xin = xle[kk] + c * t * t + wl
+        yin = -kth * c * t * (1.0 - t * t)
         nodes[0, kk] = xin[None, :] + far * sj[:, None] * dx[None, :]
         nodes[1, kk] = yin[None, :] + far * sj[:, None] * dy[None, :]
         nodes[2, kk] = z[kk]
