@@ -8,10 +8,10 @@
 namespace fpk {
 
 constexpr int kThreads = 256;        // threads per sweep CTA (faces per chunk x lines per tile)
-constexpr int kCellFields = 18;      // per-cell values staged in shared memory
+constexpr int kCellFields = 17;      // per-cell values staged in shared memory
 constexpr int kFaceFields = 10;      // per-face values staged in shared memory (W, delta)
-constexpr int kNextFields = 9;       // next chunk's cell loads staged per thread (Q, k, 1/J)
-constexpr int kEpiFields = 16;       // epilogue operands staged per thread
+constexpr int kNextFields = 15;      // staged per thread: next chunk's cell (Q, k, 1/J), face metrics x2
+constexpr int kEpiFields = 13;       // epilogue operands staged per thread (accumulator, Q^n, dk)
 constexpr int kRing = 3 * kThreads;  // shared-memory stride of one staged field (2S slots x TT lines, padded)
 
 // Shared-memory field indices of a staged cell.
@@ -21,11 +21,10 @@ enum : int {
   CF_INVJ = 8,   // 1/J
   CF_RINV = 9,   // 1/rho
   CF_U = 10,     // 10..12 velocity
-  CF_P = 13,     // pressure
-  CF_H = 14,     // total enthalpy
-  CF_SQR = 15,   // sqrt(rho)
-  CF_UC = 16,    // contravariant velocity u . grad(d), grad(d) = J k
-  CF_AC = 17     // c |grad(d)|
+  CF_H = 13,     // total enthalpy
+  CF_SQR = 14,   // sqrt(rho)
+  CF_UC = 15,    // contravariant velocity u . grad(d), grad(d) = J k
+  CF_AC = 16     // c |grad(d)|
 };
 
 enum : int { MODE_WRITE = 0, MODE_ADD = 1, MODE_RHS = 2, MODE_RK = 3 };

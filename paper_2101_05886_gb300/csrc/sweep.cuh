@@ -51,7 +51,11 @@ template <> struct Num<double> {
 template <> struct Num<float> {
   static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
   static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float sqrt_(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  }
   static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
   static __device__ __forceinline__ float ld(const void *p, long long i) {
     return __ldg(static_cast<const float *>(p) + i);
@@ -242,7 +246,6 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
       cp[(CF_U + 0) * kRing] = u0;
       cp[(CF_U + 1) * kRing] = u1;
       cp[(CF_U + 2) * kRing] = u2;
-      cp[CF_P * kRing] = p;
       cp[CF_H * kRing] = (Q[4] + p) * rinv;
       cp[CF_SQR * kRing] = Num<T>::sqrt_(Q[0]);
       cp[CF_UC * kRing] = u0 * gx + u1 * gy + u2 * gz;
@@ -250,6 +253,13 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     };
 
     // asynchronous copy of one cell's loads into this thread's staging slots
+    // asynchronous copy of the face metric of face ff into staging slot `slot` (0/1,
+    // alternating between chunks)
+    auto prefetch_face = [&](int ff, int slot) {
+      T *dst = nsb + tid + (9 + 3 * slot) * kThreads;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) cp_async_el(dst + c * kThreads, fmet + c * fcs + (long long)(ff + 1) * fsd);
+    };
     auto prefetch_cell = [&](int x) {
       T *dst = nsb + tid;
       if (x >= -G && x < nd + G) {
@@ -300,22 +310,22 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
       if (fpform) {
         const T *dkp = static_cast<const T *>(D->dk) + qo;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          cp_async_el(dst + (10 + c) * kThreads, dkp + c * qc);
-          cp_async_el(dst + (13 + c) * kThreads, fmet + c * fcs + (long long)(x + 1) * fsd);
-        }
+        for (int c = 0; c < 3; ++c) cp_async_el(dst + (10 + c) * kThreads, dkp + c * qc);
       }
     };
 
     const int nch = (nd + 1 + S - 1) / S;
-    // prologue: the first chunk's window [a0-4, a0+S+4), a0 = -1
+    // prologue: the first chunk's window [a0-4, a0+S+4), a0 = -1, and its faces' metrics
     if (lineOK) {
+      if (tf - 1 < nd) prefetch_face(tf - 1, 0);
+      cp_async_commit();
       for (int j = tf; j < S + 8; j += S) {
         T Q[5], k[3], ij;
         fetch(-5 + j, Q, k, ij);
         stage_cell(-5 + j, Q, k, ij);
       }
     }
+    cp_async_wait_all();
     __syncthreads();
 
     for (int ch = 0; ch < nch; ++ch) {
@@ -324,6 +334,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
       const bool nextOK = lineOK && ch + 1 < nch;
       if (lineOK && a + tf >= 0 && a + tf < nd) prefetch_epilogue(a + tf);
       if (nextOK) prefetch_cell(a + S + 4 + tf);
+      if (nextOK && a + S + tf < nd) prefetch_face(a + S + tf, (ch + 1) & 1);
       cp_async_commit();
       // ---- one face per thread: face ff + 1/2 between cells ff and ff+1
       const int ff = a + tf;
@@ -336,9 +347,10 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         T Qi[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) Qi[v] = CELL(CF_Q + v, 3);
+        // face metric of this face, staged by the previous chunk (or the prologue)
         T kf[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) kf[c] = __ldg(fmet + c * fcs + (long long)(ff + 1) * fsd);
+        for (int c = 0; c < 3; ++c) kf[c] = nsb[(9 + 3 * (ch & 1) + c) * kThreads + tid];
 
         // reference face state Q* = Q_i + delta (Eqs. Q_star, QdJ_star, 1dJ at order M)
         T dl[5] = {T(0), T(0), T(0), T(0), T(0)};
@@ -450,7 +462,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
             // plain scheme: F~_m and Q~_m themselves
 #pragma unroll
             for (int v = 0; v < 5; ++v) d[v] = CELL(CF_Q + v, q);
-            const T pm = CELL(CF_P, q);
+            const T pm = g1 * (d[4] - T(0.5) * (d[1] * uB[0] + d[2] * uB[1] + d[3] * uB[2]));
             const T U = uB[0] * km[0] + uB[1] * km[1] + uB[2] * km[2];
             dF[0] = d[0] * U;
             dF[1] = d[1] * U + pm * km[0];
@@ -524,11 +536,12 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           const T mA[3] = {Qm[1], Qm[2], Qm[3]};
           const T rB = Num<T>::rcp(Qp[0]);
           const T uBp[3] = {Qp[1] * rB, Qp[2] * rB, Qp[3] * rB};
+          // k_{x+1/2} is the metric of the face this thread computed in this chunk
           T kp[3], dk[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
             dk[c] = epb[(10 + c) * kThreads + tid];
-            kp[c] = epb[(13 + c) * kThreads + tid];
+            kp[c] = nsb[(9 + 3 * (ch & 1) + c) * kThreads + tid];
           }
           T t1v[5], t2v[5];
           dflux<T>(g1, rB, uBp, uA, mA, Qm[4], pA, dQ, kp, t1v);          // [F(Q*_+) - F(Q*_-)] . k_+
