@@ -249,6 +249,11 @@ def run_gpu(args):
                 "ms_per_step": ms64 / n64, "dtype": "f64"}
         b64.close()
 
+    # ---- scheme variants on one 256^3 FP32 block: where each sits between the ALU and HBM bounds
+    variants = None
+    if args.variants and rank == 0:
+        variants = run_variants(I, B, Block, Gn, M, torch, stream)
+
     # ---- single large C-grid (512 x 384 x 512, about 100M points), FP32 and FP64 plain
     c5 = None
     if args.c5 and rank == 0:
@@ -274,7 +279,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (state %.0f MB)" % (ncells * 20 / 1e6)},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "fp64_plain_single_block": fp64,
-            "c5_single_large": c5,
+            "c5_single_large": c5, "variants_256cubed_f32": variants,
         }
         print(json.dumps(result))
     for b in blocks:
@@ -282,6 +287,37 @@ def run_gpu(args):
     batch.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_variants(I, B, Block, Gn, M, torch, stream, nsteps=5):
+    """FP32 RK3 steps on one 256^3 wavy block (Mach 0.8 + vortex) for the paper's
+    characteristic WENO5-JS, the linear-upwind scheme and component-wise WENO5-JS."""
+    g = I.periodic_wavy_3d((256, 256, 256), L=10.0, amp=0.08, Gn=Gn)
+    qinf = I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0)
+    q0 = I.vortex_3d(g, mach=0.8, eps=5.0, L=10.0)
+    ncell = 256 ** 3
+    out = {}
+    for name, scheme, charw in (("weno5_char", B.FP_WENO5_JS, 1), ("lu5_char", B.FP_LINEAR_UPWIND5, 1),
+                                ("weno5_comp", B.FP_WENO5_JS, 0)):
+        blk = Block(g, metric_order=M, scheme=scheme, characteristic=charw, precision=B.FP_F32_MIXED,
+                    q_inf=qinf)
+        q = blk.to_device(q0)
+        dt = blk.cfl_dt(q, 0.5)
+        blk.rk3_step(q, dt)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(nsteps):
+            blk.rk3_step(q, dt)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        v = ncell * 3 * nsteps / (ms * 1e-3) / 1e6
+        gbs = v * 1e6 * BYTES_PER_CELL_STAGE_F32 / 1e9
+        out[name] = {"value": round(v, 1), "unit": "Mcell/s", "hbm_algorithmic_gbs": round(gbs, 1),
+                     "hbm_frac": round(gbs / peaks()[0], 4)}
+        blk.close()
+    return out
 
 
 def run_c5(args, I, B, Block, Gn, M, torch, stream):
@@ -384,6 +420,7 @@ def main():
     ap.add_argument("--blocks", type=int, default=64, help="blocks of the workload (64 = the full workload)")
     ap.add_argument("--c5", type=int, default=1, help="also time the single 100M-point C-grid (1/0)")
     ap.add_argument("--c5-steps", type=int, default=10)
+    ap.add_argument("--variants", type=int, default=1, help="also time scheme variants on a 256^3 block (1/0)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -64,6 +64,10 @@ typedef struct {
   int bc[3][2];               /* per direction (lo, hi): FP_BC_PERIODIC | FP_BC_FARFIELD | FP_BC_EXTRAP */
   double gamma;               /* ratio of specific heats (Sec. 2.1 Eq. EOS: 1.4) */
   double q_inf[5];            /* far-field state; also the reference state of the FP32 form */
+  int global_lf;              /* 0 = local Lax-Friedrichs speeds (max over the 6-point stencil),
+                                 1 = global speeds (max over the block, per direction and
+                                 characteristic field, refreshed every RK stage); Sec. 4 uses
+                                 global splitting for its shock cases */
 } fp_grid_desc;
 
 typedef struct fp_ctx fp_ctx;

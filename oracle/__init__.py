@@ -37,7 +37,8 @@ def build(force: bool = False) -> str:
 class Cfg(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int), ("n", ctypes.c_int * 3), ("M", ctypes.c_int),
                 ("scheme", ctypes.c_int), ("fp", ctypes.c_int), ("charwise", ctypes.c_int),
-                ("form", ctypes.c_int), ("bc", (ctypes.c_int * 2) * 3), ("gamma", ctypes.c_double),
+                ("form", ctypes.c_int), ("global_lf", ctypes.c_int), ("bc", (ctypes.c_int * 2) * 3),
+                ("gamma", ctypes.c_double),
                 ("qinf", ctypes.c_double * 5)]
 
 
@@ -60,6 +61,7 @@ def lib():
         L.or_metrics.argtypes = [ctypes.POINTER(Cfg), _D, ctypes.c_int, _D]
         L.or_metrics.restype = ctypes.c_int
         L.or_face_flux.argtypes = [ctypes.POINTER(Cfg), _D, _D, _D]
+        L.or_face_flux_lam.argtypes = [ctypes.POINTER(Cfg), _D, _D, _D, _D]
         L.or_rhs.argtypes = [ctypes.POINTER(Cfg), _D, _D, _D, _D]
         L.or_rhs.restype = ctypes.c_int
         L.or_rk3_step.argtypes = [ctypes.POINTER(Cfg), _D, _D, ctypes.c_double]
@@ -76,7 +78,7 @@ def _p(a: np.ndarray):
 
 
 def make_cfg(dims, n, M=6, scheme=0, fp=1, charwise=1, form=2, bc=((0, 0), (0, 0), (0, 0)),
-             gamma=1.4, qinf=(1.4, 0.0, 0.0, 0.0, 2.5)) -> Cfg:
+             gamma=1.4, qinf=(1.4, 0.0, 0.0, 0.0, 2.5), global_lf=0) -> Cfg:
     c = Cfg()
     c.dims = dims
     for d in range(3):
@@ -84,16 +86,17 @@ def make_cfg(dims, n, M=6, scheme=0, fp=1, charwise=1, form=2, bc=((0, 0), (0, 0
         c.bc[d][0] = int(bc[d][0])
         c.bc[d][1] = int(bc[d][1])
     c.M, c.scheme, c.fp, c.charwise, c.form = M, scheme, fp, charwise, form
+    c.global_lf = global_lf
     c.gamma = gamma
     for v in range(5):
         c.qinf[v] = float(qinf[v])
     return c
 
 
-def cfg_for(grid, M=6, scheme=0, fp=1, charwise=1, form=2, gamma=1.4, qinf=None) -> Cfg:
+def cfg_for(grid, M=6, scheme=0, fp=1, charwise=1, form=2, gamma=1.4, qinf=None, global_lf=0) -> Cfg:
     if qinf is None:
         qinf = (1.4, 0.0, 0.0, 0.0, 2.5)
-    return make_cfg(grid.dims, grid.n, M, scheme, fp, charwise, form, grid.bc, gamma, qinf)
+    return make_cfg(grid.dims, grid.n, M, scheme, fp, charwise, form, grid.bc, gamma, qinf, global_lf)
 
 
 def ghost(M: int) -> int:
@@ -174,4 +177,13 @@ def face_flux(cfg: Cfg, q8: np.ndarray, met8: np.ndarray) -> np.ndarray:
     out = np.zeros(5)
     lib().or_face_flux(ctypes.byref(cfg), _p(np.ascontiguousarray(q8, dtype=np.float64)),
                        _p(np.ascontiguousarray(met8, dtype=np.float64)), _p(out))
+    return out
+
+
+def face_flux_lam(cfg: Cfg, q8: np.ndarray, met8: np.ndarray, lam) -> np.ndarray:
+    """Face flux with given (global) Lax-Friedrichs speeds per characteristic field."""
+    out = np.zeros(5)
+    lib().or_face_flux_lam(ctypes.byref(cfg), _p(np.ascontiguousarray(q8, dtype=np.float64)),
+                           _p(np.ascontiguousarray(met8, dtype=np.float64)),
+                           _p(np.ascontiguousarray(lam, dtype=np.float64)), _p(out))
     return out

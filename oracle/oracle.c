@@ -385,7 +385,20 @@ static void point_eigs(const double Q[5], const double km[3], double invJ, doubl
 /* ------------------------------------------------------------------------ */
 /* The face flux F'_{i+1/2} (Sec. 3.2) from the 8 cells i-3..i+4.            */
 /* ------------------------------------------------------------------------ */
+static void face_flux_impl(const or_cfg *c, const double q8[40], const double met8[32],
+                           const double *lam_given, double out[5]);
+
 void or_face_flux(const or_cfg *c, const double q8[40], const double met8[32], double out[5]) {
+  face_flux_impl(c, q8, met8, NULL, out);
+}
+
+void or_face_flux_lam(const or_cfg *c, const double q8[40], const double met8[32], const double lam[5],
+                      double out[5]) {
+  face_flux_impl(c, q8, met8, lam, out);
+}
+
+static void face_flux_impl(const or_cfg *c, const double q8[40], const double met8[32],
+                           const double *lam_given, double out[5]) {
   const int M = c->M;
   const double gamma = c->gamma;
   const int i0 = 3;                     /* position of cell i in the 8-cell window */
@@ -445,9 +458,12 @@ void or_face_flux(const or_cfg *c, const double q8[40], const double met8[32], d
   } else {
     for (int r = 0; r < 25; ++r) { Lm[r] = (r % 6 == 0) ? 1.0 : 0.0; Rm[r] = Lm[r]; }
   }
-  /* local Lax-Friedrichs speeds: max over the stencil cells of |eigenvalue| (Sec. 4: local LF) */
+  /* local Lax-Friedrichs speeds: max over the stencil cells of |eigenvalue| (Sec. 4: local LF),
+     or the global speeds passed in */
   double lam[5] = {0, 0, 0, 0, 0};
-  for (int s = 0; s < 6; ++s) {
+  if (lam_given)
+    for (int v = 0; v < 5; ++v) lam[v] = lam_given[v];
+  for (int s = 0; s < 6 && !lam_given; ++s) {
     int m = s + 1;
     double km[3] = {met8[m * 4 + 0], met8[m * 4 + 1], met8[m * 4 + 2]};
     double e[5];
@@ -540,6 +556,26 @@ int or_rhs(const or_cfg *c, const double *met, const double *q, double *R, doubl
   double *Rl = (double *)calloc(5 * nc, sizeof(double));
   for (int d = 0; d < c->dims; ++d) {
     int nd = c->n[d];
+    /* global Lax-Friedrichs (Sec. 4: used for the shock cases): the max of |eigenvalue|
+       over every interior point of the block, per characteristic field */
+    double glam[5] = {0, 0, 0, 0, 0};
+    if (c->global_lf) {
+      for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < nj; ++j)
+          for (int i = 0; i < ni; ++i) {
+            size_t o = at3(&A, i, j, k);
+            double Q[5], km[3], e[5];
+            for (int v = 0; v < 5; ++v) Q[v] = g[(size_t)v * nb + o];
+            for (int a2 = 0; a2 < 3; ++a2) km[a2] = met[(size_t)(3 * d + a2) * nb + o];
+            point_eigs(Q, km, met[(size_t)9 * nb + o], c->gamma, e);
+            if (c->charwise) {
+              for (int v = 0; v < 5; ++v) if (fabs(e[v]) > glam[v]) glam[v] = fabs(e[v]);
+            } else {
+              double mx = fabs(e[0]) > fabs(e[4]) ? fabs(e[0]) : fabs(e[4]);
+              for (int v = 0; v < 5; ++v) if (mx > glam[v]) glam[v] = mx;
+            }
+          }
+    }
     double *Fline = (double *)malloc((size_t)(nd + 1) * 5 * sizeof(double));
     int t1 = (d == 0) ? 1 : 0, t2 = (d == 2) ? 1 : 2;   /* transverse directions */
     for (int b = 0; b < c->n[t2]; ++b)
@@ -559,7 +595,8 @@ int or_rhs(const or_cfg *c, const double *met, const double *q, double *R, doubl
             for (int a2 = 0; a2 < 3; ++a2) met8[m * 4 + a2] = met[(size_t)(3 * d + a2) * nb + o];
             met8[m * 4 + 3] = met[(size_t)9 * nb + o];
           }
-          or_face_flux(c, q8, met8, Fline + (size_t)(f + 1) * 5);
+          if (c->global_lf) or_face_flux_lam(c, q8, met8, glam, Fline + (size_t)(f + 1) * 5);
+          else or_face_flux(c, q8, met8, Fline + (size_t)(f + 1) * 5);
         }
         for (int i = 0; i < nd; ++i) {                  /* Eq. (aderivative) with Delta xi = 1 */
           int p[3];

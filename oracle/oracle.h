@@ -31,6 +31,7 @@ typedef struct {
   int fp;          /* 1 = free-stream-preserving form, 0 = plain scheme */
   int charwise;    /* 1 = characteristic-wise (Roe eigenvectors), 0 = component-wise */
   int form;        /* 2 = WENO(F_m - F*_m + F*_face) (Eq. my_point2), 1 = WENO(F_m - F*_m) + F*_face (Eq. my_point1) */
+  int global_lf;   /* 0 = local Lax-Friedrichs speeds (stencil max), 1 = global (max over the block) */
   int bc[3][2];    /* 0 periodic, 1 far field (q_inf), 2 zero gradient */
   double gamma;
   double qinf[5];
@@ -47,6 +48,9 @@ int or_metrics(const or_cfg *c, const double *nodes, int Gn, double *met);
 /* face flux at i+1/2 from 8 consecutive cells i-3..i+4 along one direction d:
    q8 [8][5], met8 [8][4] = (k_x, k_y, k_z, 1/J) of that direction */
 void or_face_flux(const or_cfg *c, const double q8[40], const double met8[32], double out[5]);
+/* as or_face_flux with the Lax-Friedrichs speeds lam[5] given (global splitting) */
+void or_face_flux_lam(const or_cfg *c, const double q8[40], const double met8[32], const double lam[5],
+                      double out[5]);
 int or_rhs(const or_cfg *c, const double *met, const double *q, double *R, double *dqdt);
 int or_rk3_step(const or_cfg *c, const double *met, double *q, double dt);
 double or_cfl_dt(const or_cfg *c, const double *met, const double *q, double cfl);

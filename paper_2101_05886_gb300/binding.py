@@ -33,7 +33,7 @@ class fp_grid_desc(ctypes.Structure):
                 ("scheme", ctypes.c_int), ("free_stream_preserving", ctypes.c_int),
                 ("characteristic", ctypes.c_int), ("precision", ctypes.c_int),
                 ("bc", (ctypes.c_int * 2) * 3), ("gamma", ctypes.c_double),
-                ("q_inf", ctypes.c_double * 5)]
+                ("q_inf", ctypes.c_double * 5), ("global_lf", ctypes.c_int)]
 
 
 _lib = None
@@ -98,7 +98,7 @@ def _check(st, ctx=None, batch=None):
 
 def make_desc(dims, n, metric_order=6, scheme=FP_WENO5_JS, fp=1, characteristic=1,
               precision=FP_F64, bc=((0, 0), (0, 0), (0, 0)), gamma=1.4,
-              q_inf=(1.4, 0.0, 0.0, 0.0, 2.5)) -> fp_grid_desc:
+              q_inf=(1.4, 0.0, 0.0, 0.0, 2.5), global_lf=0) -> fp_grid_desc:
     d = fp_grid_desc()
     d.dims = dims
     for k in range(3):
@@ -113,6 +113,7 @@ def make_desc(dims, n, metric_order=6, scheme=FP_WENO5_JS, fp=1, characteristic=
     d.gamma = gamma
     for v in range(5):
         d.q_inf[v] = float(q_inf[v])
+    d.global_lf = int(global_lf)
     return d
 
 

@@ -31,6 +31,9 @@ struct fp_ctx {
   int *status = nullptr;
   double *dt_dev = nullptr;
   unsigned long long *cfl_bits = nullptr;
+  void *lamg = nullptr;               // T [3][3] global Lax-Friedrichs speeds
+  int2 *lam_items = nullptr;          // (block 0, first point) chunks for the speed reduction
+  int nlam_items = 0;
   BlockDev hblk;
   BlockDev *dblk = nullptr;
   BlockDev uploaded;                  // last BlockDev copied to dblk
@@ -53,8 +56,10 @@ struct fp_batch {
   double dt_host = 0.0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int dims = 3, M = 6, scheme = 0, charwise = 1, fp = 1, is_f32 = 1;
+  int dims = 3, M = 6, scheme = 0, charwise = 1, fp = 1, is_f32 = 1, global_lf = 0;
   int per_sm = 1, nsm = 152;
+  int2 *lam_items = nullptr;
+  int nlam_items = 0;
   std::string err;
 };
 
@@ -146,6 +151,8 @@ void fill_dirs(fp_ctx *c) {
   for (int v = 0; v < 5; ++v) B.qbar[v] = c->desc.q_inf[v];
   B.gamma = c->desc.gamma;
   B.status = c->status;
+  B.global_lf = c->desc.global_lf;
+  B.lamg = c->lamg;
 }
 
 void make_items(const BlockDev &B, int bidx, int d, std::vector<int2> &out) {
@@ -200,6 +207,7 @@ int validate(const fp_grid_desc *d, int ghost_nodes, std::string &why) {
   if (d->precision != FP_F64 && d->precision != FP_F32_MIXED) { why = "unknown precision"; return 0; }
   if (d->free_stream_preserving != 0 && d->free_stream_preserving != 1) { why = "free_stream_preserving must be 0 or 1"; return 0; }
   if (d->characteristic != 0 && d->characteristic != 1) { why = "characteristic must be 0 or 1"; return 0; }
+  if (d->global_lf != 0 && d->global_lf != 1) { why = "global_lf must be 0 or 1"; return 0; }
   for (int k = 0; k < d->dims; ++k)
     for (int s = 0; s < 2; ++s)
       if (d->bc[k][s] < 0 || d->bc[k][s] > 2) { why = "unknown boundary code"; return 0; }
@@ -241,6 +249,7 @@ void fp_free(fp_ctx *c) {
   for (int d = 0; d < 3; ++d) { cudaFree(c->fmet[d]); cudaFree(c->dk[d]); cudaFree(c->items[d]); }
   cudaFree(c->q1); cudaFree(c->q2); cudaFree(c->racc);
   cudaFree(c->status); cudaFree(c->dt_dev); cudaFree(c->cfl_bits); cudaFree(c->dblk);
+  cudaFree(c->lamg); cudaFree(c->lam_items);
   delete c;
 }
 
@@ -334,6 +343,16 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
   FP_TRY(cudaMalloc(&c->dt_dev, sizeof(double)), "cudaMalloc(dt)");
   FP_TRY(cudaMalloc(&c->cfl_bits, sizeof(unsigned long long)), "cudaMalloc(cfl)");
   FP_TRY(cudaMalloc(&c->dblk, sizeof(BlockDev)), "cudaMalloc(block)");
+  FP_TRY(cudaMalloc(&c->lamg, 9 * c->esize), "cudaMalloc(global speeds)");
+  FP_TRY(cudaMemset(c->lamg, 0, 9 * c->esize), "clear global speeds");
+  {
+    std::vector<int2> li;
+    for (long long p0 = 0; p0 < c->ncells; p0 += fpk::kLamChunk) li.push_back(make_int2(0, (int)p0));
+    c->nlam_items = (int)li.size();
+    FP_TRY(cudaMalloc(&c->lam_items, li.size() * sizeof(int2)), "cudaMalloc(speed items)");
+    FP_TRY(cudaMemcpy(c->lam_items, li.data(), li.size() * sizeof(int2), cudaMemcpyHostToDevice),
+           "copy speed items");
+  }
   fill_dirs(c);
   c->per_sm = prepare(c->is_f32, M, desc->scheme);
   FP_TRY(cudaGetLastError(), "prepare sweep kernels");
@@ -347,6 +366,11 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
 static int run_passes(fp_ctx *c, int rk, cudaStream_t s) {
   const int dims = c->desc.dims, M = c->desc.metric_order;
   for (int stage = 0; stage < (rk ? 3 : 1); ++stage) {
+    if (c->desc.global_lf) {
+      cudaError_t e = fpk::launch_lambda(c->dblk, 1, c->lam_items, c->nlam_items, c->is_f32,
+                                         c->desc.characteristic, stage, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "global speed launch");
+    }
     for (int d = 0; d < dims; ++d) {
       fpk::SweepLaunch L;
       L.blocks = c->dblk;
@@ -458,8 +482,8 @@ int fp_get_device_status(fp_ctx *c, void *stream) {
   return FP_OK;
 }
 
-int fp_launches_per_rhs(const fp_ctx *c) { return c ? c->desc.dims : 0; }
-int fp_launches_per_step(const fp_ctx *c) { return c ? 3 * c->desc.dims : 0; }
+int fp_launches_per_rhs(const fp_ctx *c) { return c ? c->desc.dims + (c->desc.global_lf ? 2 : 0) : 0; }
+int fp_launches_per_step(const fp_ctx *c) { return c ? 3 * fp_launches_per_rhs(c) : 0; }
 
 int fp_get_tile(const fp_ctx *c, int dir, int *faces, int *lines) {
   if (!c || dir < 0 || dir > 2 || !faces || !lines) return FP_ERR_ARG;
@@ -488,12 +512,13 @@ void fp_batch_free(fp_batch *b) {
   cudaFree(b->dblk);
   for (int d = 0; d < 3; ++d) cudaFree(b->items[d]);
   cudaFree(b->dt_dev);
+  cudaFree(b->lam_items);
   delete b;
 }
 
 const char *fp_batch_last_error(const fp_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
-int fp_batch_launches_per_step(const fp_batch *b) { return b ? 3 * b->dims : 0; }
+int fp_batch_launches_per_step(const fp_batch *b) { return b ? 3 * (b->dims + (b->global_lf ? 2 : 0)) : 0; }
 
 static int batch_items(fp_batch *b, int d, const std::vector<int> *only_blocks) {
   std::vector<std::pair<long long, int2>> work;
@@ -601,7 +626,7 @@ int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int
     const fp_grid_desc &d = blocks[k]->desc;
     if (d.dims != d0.dims || d.metric_order != d0.metric_order || d.scheme != d0.scheme ||
         d.precision != d0.precision || d.characteristic != d0.characteristic ||
-        d.free_stream_preserving != d0.free_stream_preserving)
+        d.free_stream_preserving != d0.free_stream_preserving || d.global_lf != d0.global_lf)
       return FP_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
@@ -609,6 +634,7 @@ int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int
   b->dims = d0.dims; b->M = d0.metric_order; b->scheme = d0.scheme;
   b->charwise = d0.characteristic; b->fp = d0.free_stream_preserving;
   b->is_f32 = d0.precision == FP_F32_MIXED;
+  b->global_lf = d0.global_lf;
   b->per_sm = blocks[0]->per_sm;
   b->nsm = blocks[0]->nsm;
   for (int k = 0; k < nblocks; ++k) {
@@ -622,6 +648,16 @@ int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int
   if (e == cudaSuccess) e = cudaMalloc(&b->dt_dev, sizeof(double));
   if (e == cudaSuccess) e = cudaMemsetAsync(b->dt_dev, 0, sizeof(double), s);
   if (e != cudaSuccess) { fp_batch_free(b); return FP_ERR_OOM; }
+  {
+    std::vector<int2> li;
+    for (int k = 0; k < nblocks; ++k)
+      for (long long p0 = 0; p0 < blocks[k]->ncells; p0 += fpk::kLamChunk) li.push_back(make_int2(k, (int)p0));
+    b->nlam_items = (int)li.size();
+    e = cudaMalloc(&b->lam_items, li.size() * sizeof(int2));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->lam_items, li.data(), li.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { fp_batch_free(b); return FP_ERR_CUDA; }
+  }
   int st = FP_OK;
   if (autotune) st = batch_autotune(b, s);
   if (!st) st = batch_upload(b, s);
@@ -633,11 +669,17 @@ int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int
   if (e != cudaSuccess) { fp_batch_free(b); return FP_ERR_CUDA; }
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (int stage = 0; stage < 3 && !st; ++stage)
+    for (int stage = 0; stage < 3 && !st; ++stage) {
+      if (b->global_lf) {
+        cudaError_t el = fpk::launch_lambda(b->dblk, (int)b->hblk.size(), b->lam_items, b->nlam_items,
+                                            b->is_f32, b->charwise, stage, cs);
+        if (el != cudaSuccess) st = bfail(b, FP_ERR_CUDA, "batch speed launch");
+      }
       for (int d = 0; d < b->dims && !st; ++d) {
         int mode = d == 0 ? fpk::MODE_WRITE : (d == b->dims - 1 ? fpk::MODE_RK : fpk::MODE_ADD);
         st = batch_pass(b, d, mode, stage, cs);
       }
+    }
     cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
     if (e == cudaSuccess) e = e2;
   }
@@ -672,6 +714,11 @@ int fp_batch_rhs(fp_batch *b, void *const *dqdt_devs, void *stream) {
     b->hblk[k].dqdt = dqdt_devs[k];
   }
   int st = batch_upload(b, s);
+  if (!st && b->global_lf) {
+    cudaError_t el = fpk::launch_lambda(b->dblk, (int)b->hblk.size(), b->lam_items, b->nlam_items, b->is_f32,
+                                        b->charwise, 0, s);
+    if (el != cudaSuccess) st = bfail(b, FP_ERR_CUDA, "batch speed launch");
+  }
   for (int d = 0; d < b->dims && !st; ++d) {
     int mode = d == 0 ? fpk::MODE_WRITE : (d == b->dims - 1 ? fpk::MODE_RHS : fpk::MODE_ADD);
     st = batch_pass(b, d, mode, 0, s);
@@ -739,6 +786,10 @@ extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream
   e = cudaMemcpyAsync(S.blk, &b, sizeof(BlockDev), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: descriptor upload");
   const int dims = c->desc.dims, M = c->desc.metric_order;
+  if (c->desc.global_lf) {
+    e = fpk::launch_lambda(S.blk, 1, c->lam_items, c->nlam_items, c->is_f32, c->desc.characteristic, 0, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: global speed launch");
+  }
   for (int d = 0; d < dims; ++d) {
     fpk::SweepLaunch L;
     L.blocks = S.blk;

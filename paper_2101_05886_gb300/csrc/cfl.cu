@@ -50,7 +50,87 @@ __global__ void k_cfl(const BlockDev *blk, long long ncells, int ni, int nj, int
   if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(red[0]));
 }
 
+template <typename T>
+__global__ void k_lam_zero(const BlockDev *blocks, int nblocks) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nblocks) {
+    T *l = static_cast<T *>(blocks[b].lamg);
+    for (int t = 0; t < 9; ++t) l[t] = T(0);
+  }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(float *a, float v) {
+  atomicMax(reinterpret_cast<unsigned int *>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_nonneg(double *a, double v) {
+  atomicMax(reinterpret_cast<unsigned long long *>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+// per item: max over its points of |U - c|grad d||, |U|, |U + c|grad d|| for every direction
+template <typename T>
+__global__ void k_lam_max(const BlockDev *blocks, const int2 *items, int nitems, int charwise, int stage) {
+  __shared__ T red[9][256];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 item = items[it];
+    const BlockDev *B = blocks + item.x;
+    const int dims = B->dims, ni = B->dir[0].nd, nj = B->dir[1].nd;
+    const long long qc = B->qc, mc = B->mc;
+    const T *q = static_cast<const T *>(B->q[stage]);
+    const T *met = static_cast<const T *>(B->met);
+    const T g = T(B->gamma);
+    T best[9];
+    for (int t = 0; t < 9; ++t) best[t] = T(0);
+    const long long end = min((long long)item.y + kLamChunk, qc);
+    for (long long idx = (long long)item.y + threadIdx.x; idx < end; idx += blockDim.x) {
+      const int i = (int)(idx % ni);
+      const long long r = idx / ni;
+      const int j = (int)(r % nj);
+      const int k = (int)(r / nj);
+      const long long mo = B->moff + i + j * B->dir[0].mT1 + (dims == 3 ? k * B->dir[0].mT2 : 0);
+      const T rho = q[idx], rinv = T(1) / rho;
+      const T u = q[qc + idx] * rinv, v = q[2 * qc + idx] * rinv, w = q[3 * qc + idx] * rinv;
+      const T p = (g - T(1)) * (q[4 * qc + idx] - T(0.5) * rho * (u * u + v * v + w * w));
+      const T c = sqrt(g * p * rinv);
+      const T Jc = T(1) / met[9 * mc + mo];
+      for (int d = 0; d < dims; ++d) {
+        const T gx = Jc * met[(3 * d) * mc + mo], gy = Jc * met[(3 * d + 1) * mc + mo],
+                gz = Jc * met[(3 * d + 2) * mc + mo];
+        const T U = u * gx + v * gy + w * gz, a = c * sqrt(gx * gx + gy * gy + gz * gz);
+        T lm = fabs(U - a), l0 = fabs(U), lp = fabs(U + a);
+        if (!charwise) { lm = fmax(lm, lp); l0 = lm; lp = lm; }
+        best[3 * d] = fmax(best[3 * d], lm);
+        best[3 * d + 1] = fmax(best[3 * d + 1], l0);
+        best[3 * d + 2] = fmax(best[3 * d + 2], lp);
+      }
+    }
+    for (int t = 0; t < 9; ++t) red[t][threadIdx.x] = best[t];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+      if (threadIdx.x < h)
+        for (int t = 0; t < 9; ++t) red[t][threadIdx.x] = fmax(red[t][threadIdx.x], red[t][threadIdx.x + h]);
+      __syncthreads();
+    }
+    if (threadIdx.x < 3 * dims) atomic_max_nonneg(static_cast<T *>(B->lamg) + threadIdx.x, red[threadIdx.x][0]);
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_lambda(const BlockDev *blocks, int nblocks, const int2 *items, int nitems, int is_f32,
+                          int charwise, int stage, cudaStream_t s) {
+  const int zb = (nblocks + 127) / 128;
+  int grid = nitems < 152 * 8 ? nitems : 152 * 8;
+  if (grid < 1) grid = 1;
+  if (is_f32) {
+    k_lam_zero<float><<<zb, 128, 0, s>>>(blocks, nblocks);
+    k_lam_max<float><<<grid, 256, 0, s>>>(blocks, items, nitems, charwise, stage);
+  } else {
+    k_lam_zero<double><<<zb, 128, 0, s>>>(blocks, nblocks);
+    k_lam_max<double><<<grid, 256, 0, s>>>(blocks, items, nitems, charwise, stage);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cfl(const BlockDev *blk, int is_f32, long long ncells, const int *n, int dims,
                        unsigned long long *out_bits, cudaStream_t s) {

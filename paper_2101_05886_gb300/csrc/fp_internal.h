@@ -59,6 +59,8 @@ struct BlockDev {
   double qbar[5];      // reference state (far-field state)
   double gamma;
   int *status;         // device status word: bit0 non-finite state
+  int global_lf;       // 1: Lax-Friedrichs speeds from lamg instead of the stencil
+  void *lamg;          // T [3 directions][3]: max |U - c|grad||, |U|, |U + c|grad|| over the block
 };
 
 struct SweepLaunch {
@@ -94,6 +96,12 @@ struct MetricJob {
 };
 cudaError_t build_metrics(const MetricJob &J, cudaStream_t s);
 cudaError_t convert_f64_to_f32(const double *src, float *dst, long long n, cudaStream_t s);
+
+// Global Lax-Friedrichs speeds (cfl.cu): zero, then max over (block, first point) items of
+// kLamChunk points each.
+constexpr int kLamChunk = 8192;
+cudaError_t launch_lambda(const BlockDev *blocks, int nblocks, const int2 *items, int nitems,
+                          int is_f32, int charwise, int stage, cudaStream_t s);
 
 // CFL reduction (cfl.cu).
 cudaError_t launch_cfl(const BlockDev *blk, int is_f32, long long ncells, const int *n, int dims,

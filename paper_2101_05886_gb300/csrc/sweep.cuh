@@ -186,6 +186,8 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     const T *__restrict__ fmet = static_cast<const T *>(D->fmet) + fbase;
     const T *__restrict__ qin = static_cast<const T *>(B->q[stage]);
     const T g1 = T(B->gamma - 1.0), gam = T(B->gamma);
+    const int glf = B->global_lf;
+    const T *lamg = glf ? static_cast<const T *>(B->lamg) + 3 * dir : nullptr;
     T qb[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qb[v] = T(B->qbar[v]);
@@ -377,14 +379,18 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         const T ps = g1 * (Qs[4] - T(0.5) * (Qs[1] * us[0] + Qs[2] * us[1] + Qs[3] * us[2]));
         const T ms[3] = {Qs[1], Qs[2], Qs[3]};
 
-        // local Lax-Friedrichs speeds over the stencil cells i-2..i+3
+        // Lax-Friedrichs speeds: local (max over the stencil cells i-2..i+3) or global
         T lm = T(0), l0 = T(0), lp = T(0);
+        if (glf) {
+          lm = lamg[0]; l0 = lamg[1]; lp = lamg[2];
+        } else {
 #pragma unroll
-        for (int q = 1; q <= 6; ++q) {
-          const T U = CELL(CF_UC, q), ac = CELL(CF_AC, q);
-          lm = fmax(lm, fabs(U - ac));
-          l0 = fmax(l0, fabs(U));
-          lp = fmax(lp, fabs(U + ac));
+          for (int q = 1; q <= 6; ++q) {
+            const T U = CELL(CF_UC, q), ac = CELL(CF_AC, q);
+            lm = fmax(lm, fabs(U - ac));
+            l0 = fmax(l0, fabs(U));
+            lp = fmax(lp, fabs(U + ac));
+          }
         }
         T lam[5];
         if (charwise) {

@@ -148,6 +148,22 @@ def paper_random_2d(npts=21, L=20.0, frac=0.2, seed=7, Gn=6):
     return Grid(2, (n, n, 1), Gn, nodes, (bc, bc, (0, 0)), "paper_random_2d")
 
 
+def random_grid_2d(n, L=1.0, frac=0.2, seed=5, Gn=6):
+    """Cartesian grid of n x n points on [0,L]^2 with every node (ghosts included)
+    moved by frac*spacing in a seeded random direction (the randomised grids of the
+    shock tests of Sec. 4.2); zero-gradient boundaries."""
+    rng = np.random.default_rng(seed)
+    h = L / (n - 1)
+    I = _index_range(n, Gn)
+    JJ, II = np.meshgrid(I, I, indexing="ij")
+    ang = rng.uniform(0.0, 2 * np.pi, size=II.shape)
+    x = h * II + frac * h * np.cos(ang)
+    y = h * JJ + frac * h * np.sin(ang)
+    nodes = np.ascontiguousarray(np.stack([x, y]))
+    bc = (BC_EXTRAP, BC_EXTRAP)
+    return Grid(2, (n, n, 1), Gn, nodes, (bc, bc, (0, 0)), "random_grid_2d")
+
+
 def extrude_2d(g2: Grid, nk: int, dz: float = 1.0):
     """Extrude a 2-D grid into 3-D with z = dz*k (periodic in k): used to check that
     the 3-D operators reduce to the 2-D ones."""
@@ -382,6 +398,24 @@ def vortex_3d(grid: Grid, mach=0.8, eps=5.0, L=10.0, gamma=GAMMA):
     centred in the x-y plane of the box."""
     x, y, _ = grid.interior_xyz()
     return shu_vortex(x, y, 0.0, 0.5 * L, 0.5 * L, eps=eps, mach=mach, L=L, gamma=gamma)
+
+
+def normal_shock_state(grid: Grid, x0, mach=2.0, gamma=GAMMA):
+    """Planar shock at x = x0 moving into still gas (rho = gamma, p = 1, c = 1) with
+    shock Mach number `mach`; the Rankine-Hugoniot post-shock state is behind it
+    (x < x0)."""
+    x = grid.interior_xyz()[0]
+    r1, p1 = gamma, 1.0
+    m2 = mach * mach
+    r2 = r1 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    p2 = p1 * (2.0 * gamma * m2 - (gamma - 1.0)) / (gamma + 1.0)
+    u2 = mach * 1.0 * (1.0 - r1 / r2)
+    behind = x < x0
+    rho = np.where(behind, r2, r1)
+    u = np.where(behind, u2, 0.0)
+    p = np.where(behind, p2, p1)
+    z = np.zeros_like(rho)
+    return primitive_to_conserved(rho, u, z, z, p, gamma)
 
 
 def perturbed_state(grid: Grid, qinf, amp=1e-3, seed=0):

@@ -15,7 +15,7 @@ def _stream():
 
 class Block:
     def __init__(self, grid, metric_order=6, scheme=B.FP_WENO5_JS, fp=1, characteristic=1,
-                 precision=B.FP_F64, gamma=1.4, q_inf=(1.4, 0.0, 0.0, 0.0, 2.5)):
+                 precision=B.FP_F64, gamma=1.4, q_inf=(1.4, 0.0, 0.0, 0.0, 2.5), global_lf=0):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         self.grid = grid
@@ -25,7 +25,7 @@ class Block:
         self.precision = precision
         self.dtype = torch.float32 if precision == B.FP_F32_MIXED else torch.float64
         self.desc = B.make_desc(grid.dims, grid.n, metric_order, scheme, fp, characteristic,
-                                precision, grid.bc, gamma, q_inf)
+                                precision, grid.bc, gamma, q_inf, global_lf)
         nodes = np.ascontiguousarray(grid.nodes, dtype=np.float64)
         self.ctx = B.fp_init_grid(self.desc, nodes.ctypes.data, int(grid.Gn), _stream())
         self.G = B.fp_ghost_width(metric_order)

@@ -302,3 +302,52 @@ def test_full_size_256cubed_sampled_parity(precision, tol):
         err = max(np.abs(got[c] - ref[c]).max() / full_scale[c] for c in range(5))
         assert err <= tol, (lo, err, [np.abs(got[c] - ref[c]).max() / full_scale[c] for c in range(5)])
     blk.close()
+
+
+# ---------------------------------------------------------------- global Lax-Friedrichs
+@pytest.mark.parametrize("name,M,scheme,precision,tol", [("3d_vortex", 6, 0, F64, 1e-12), ("3d_ogrid", 4, 1, F64, 1e-12),
+                                                         ("2d_vortex", 8, 0, F64, 1e-12), ("3d_vortex", 6, 0, F32, 1e-5)])
+def test_global_lax_friedrichs_parity(name, M, scheme, precision, tol):
+    g, qinf, q = _case(name, M)
+    if precision == F32:
+        q = q.astype(np.float32).astype(np.float64)
+    blk = Block(g, metric_order=M, scheme=scheme, precision=precision, q_inf=qinf, global_lf=1)
+    dq = blk.rhs(blk.to_device(q)).cpu().numpy()
+    cfg = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf, global_lf=1)
+    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q)
+    errs = rel_err(dq, dqo, per_component=True)
+    assert max(errs) <= tol, errs
+    # the global splitting is more dissipative: it differs from the local one
+    cfl = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf)
+    _, dql = O.rhs(cfl, O.metrics(cfl, g.nodes, g.Gn), q)
+    assert rel_err(dql, dqo) > 1e-6
+    blk.close()
+
+
+@pytest.mark.parametrize("frac", [0.05, 0.2])
+def test_shock_on_randomised_grid_parity_and_no_overshoot(frac):
+    """Mach 2 planar shock on a randomised grid (Sec. 4.2 shock cases): global LF
+    WENO5-JS FP, FP64; GPU and oracle agree over a few RK3 steps, and the density
+    stays within the two shock states (no spurious oscillations)."""
+    M = 6
+    g = I.random_grid_2d(48, L=1.0, frac=frac, seed=5, Gn=O.node_ghost(M))
+    q = I.normal_shock_state(g, 0.3, mach=2.0)
+    qinf = q[:, 0, 0, -1]
+    blk = Block(g, metric_order=M, precision=F64, q_inf=qinf, global_lf=1)
+    cfg = O.cfg_for(g, M=M, qinf=qinf, global_lf=1)
+    met = O.metrics(cfg, g.nodes, g.Gn)
+    _, dqo = O.rhs(cfg, met, q)
+    qd = blk.to_device(q)
+    assert rel_err(blk.rhs(qd).cpu().numpy(), dqo) <= 1e-12
+    dt = 0.5 * O.cfl_dt(cfg, met, q, 0.5)
+    qo = q.copy()
+    for _ in range(10):
+        blk.rk3_step(qd, dt)
+        qo = O.rk3_step(cfg, met, qo, dt)
+    qg = qd.cpu().numpy()
+    assert rel_err(qg - q, qo - q) <= 1e-10
+    rho = qg[0]
+    r1, r2 = q[0].min(), q[0].max()
+    assert rho.min() > r1 - 0.05 * (r2 - r1) and rho.max() < r2 + 0.05 * (r2 - r1)
+    assert blk.status() == B.FP_OK
+    blk.close()

@@ -542,3 +542,27 @@ def test_cfl_dt_closed_form_on_cartesian_grid():
     c = 1.0
     expected = 0.7 / sum((abs(u[d]) + c) / h for d in range(3))
     assert abs(O.cfl_dt(cfg, met, I.uniform_state(g, qinf), 0.7) - expected) < 1e-14
+
+
+def test_global_speeds_enter_the_dissipation_linearly():
+    """With given (global) Lax-Friedrichs speeds the FP linear-upwind face flux is still
+    the central flux plus the dissipation of Sec. 3.1 with those speeds: doubling the
+    speeds doubles the difference to the central flux."""
+    rng = np.random.default_rng(21)
+    cfg = O.make_cfg(3, (8, 8, 8), M=6, scheme=1, fp=1)
+    c6 = np.array([1, -8, 37, 37, -8, 1]) / 60.0
+    base = _random_state(rng, mach=0.5)
+    q8 = np.array([base * (1 + 0.05 * rng.standard_normal(5)) for _ in range(8)])
+    q8[:, 0] = np.abs(q8[:, 0])
+    met8 = np.empty((8, 4))
+    k0 = rng.standard_normal(3)
+    for m in range(8):
+        met8[m, :3] = k0 + 0.1 * rng.standard_normal(3)
+        met8[m, 3] = rng.uniform(0.5, 1.5)
+    st = slice(1, 7)
+    Ft = np.array([euler_flux_k(q8[m], met8[m, :3]) for m in range(8)])
+    central = c6 @ Ft[st]
+    lam = np.array([3.0, 2.0, 2.0, 2.0, 4.0])
+    f1 = O.face_flux_lam(cfg, q8, met8, lam)
+    f2 = O.face_flux_lam(cfg, q8, met8, 2 * lam)
+    assert np.abs((f2 - central) - 2 * (f1 - central)).max() < 1e-12 * np.abs(central).max()
