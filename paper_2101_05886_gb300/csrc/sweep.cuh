@@ -62,6 +62,56 @@ template <> struct Num<float> {
   }
 };
 
+// Pairs of values processed by one instruction: packed FP32x2 arithmetic (sm_100+
+// FFMA2 / FADD2 / FMUL2) for float, two scalar operations for double.
+struct dpair { double x, y; };
+template <typename T> struct PairOf;
+template <> struct PairOf<float> { using type = float2; };
+template <> struct PairOf<double> { using type = dpair; };
+
+__device__ __forceinline__ float2 pmk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ dpair pmk(double a, double b) { return dpair{a, b}; }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ dpair pfma(dpair a, dpair b, dpair c) { return dpair{fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)}; }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ dpair padd(dpair a, dpair b) { return dpair{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ dpair pmul(dpair a, dpair b) { return dpair{a.x * b.x, a.y * b.y}; }
+template <typename P> __device__ __forceinline__ P psub(P a, P b) { return pfma(b, pmk(decltype(a.x)(-1), decltype(a.x)(-1)), a); }
+template <typename P> __device__ __forceinline__ P pc(decltype(P::x) v) { return pmk(v, v); }
+
+// Fifth-order reconstruction of a pair of five-point stencils (the + side and the
+// mirrored - side of one characteristic field) in first-difference form; returns
+// the two reconstructed values.
+template <typename T, int SCHEME>
+__device__ __forceinline__ typename PairOf<T>::type recon5_pair(
+    typename PairOf<T>::type v0, typename PairOf<T>::type v1, typename PairOf<T>::type v2,
+    typename PairOf<T>::type v3, typename PairOf<T>::type v4) {
+  using P = typename PairOf<T>::type;
+  const P a = psub(v1, v0), b = psub(v2, v1), c = psub(v3, v2), d = psub(v4, v3);
+  const P r0 = pfma(pc<P>(T(5)), b, pmul(pc<P>(T(-2)), a));      // 6 (q0 - v2)
+  const P r1 = pfma(pc<P>(T(2)), c, b);                          // 6 (q1 - v2)
+  const P r2 = pfma(pc<P>(T(4)), c, pmul(pc<P>(T(-1)), d));      // 6 (q2 - v2)
+  if (SCHEME == 1) {
+    const P s = pfma(pc<P>(T(0.3)), r2, pfma(pc<P>(T(0.6)), r1, pmul(pc<P>(T(0.1)), r0)));
+    return pfma(pc<P>(T(1.0 / 6.0)), s, v2);
+  }
+  const P d0 = psub(b, a), e0 = pfma(pc<P>(T(3)), b, pmul(pc<P>(T(-1)), a));
+  const P d1 = psub(c, b), e1 = padd(b, c);
+  const P d2 = psub(d, c), e2 = pfma(pc<P>(T(-3)), c, d);
+  const P c13 = pc<P>(T(13.0 / 12.0)), q4 = pc<P>(T(0.25)), eps = pc<P>(T(1.0e-6));
+  const P b0 = pfma(c13, pmul(d0, d0), pfma(q4, pmul(e0, e0), eps));
+  const P b1 = pfma(c13, pmul(d1, d1), pfma(q4, pmul(e1, e1), eps));
+  const P b2 = pfma(c13, pmul(d2, d2), pfma(q4, pmul(e2, e2), eps));
+  const P s0 = pmul(b0, b0), s1 = pmul(b1, b1), s2 = pmul(b2, b2);
+  const P a0 = pmul(pc<P>(T(0.1)), pmk(Num<T>::rcp(s0.x), Num<T>::rcp(s0.y)));
+  const P a1 = pmul(pc<P>(T(0.6)), pmk(Num<T>::rcp(s1.x), Num<T>::rcp(s1.y)));
+  const P a2 = pmul(pc<P>(T(0.3)), pmk(Num<T>::rcp(s2.x), Num<T>::rcp(s2.y)));
+  const P num = pfma(a2, r2, pfma(a1, r1, pmul(a0, r0)));
+  const P den = pmul(pc<P>(T(6)), padd(padd(a0, a1), a2));
+  return pfma(num, pmk(Num<T>::rcp(den.x), Num<T>::rcp(den.y)), v2);
+}
+
 // Asynchronous global -> shared copies of single elements (sm_80+ cp.async).
 template <typename T>
 __device__ __forceinline__ void cp_async_el(T *smem, const T *gmem) {
@@ -434,6 +484,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         const T h2[3] = {T(0.5) * t2[0], T(0.5) * t2[1], T(0.5) * t2[2]};
         const T hut1 = T(0.5) * ut1, hut2 = T(0.5) * ut2;
 
+        using P = typename PairOf<T>::type;
         // (1/2) l_s . d for the five characteristic fields
         auto project = [&](const T d[5], T c[5]) {
           if (!charwise) {
@@ -489,12 +540,14 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           }
         }
 #undef CELL
-        // reconstruct each field from both sides and back-project (R columns)
+        // reconstruct each field from both sides (the - side mirrored) and back-project
         T h[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          h[v] = recon5<T, SCHEME>(fpl[0][v], fpl[1][v], fpl[2][v], fpl[3][v], fpl[4][v]) +
-                 recon5<T, SCHEME>(fmi[5][v], fmi[4][v], fmi[3][v], fmi[2][v], fmi[1][v]);
+          const P r = recon5_pair<T, SCHEME>(pmk(fpl[0][v], fmi[5][v]), pmk(fpl[1][v], fmi[4][v]),
+                                             pmk(fpl[2][v], fmi[3][v]), pmk(fpl[3][v], fmi[2][v]),
+                                             pmk(fpl[4][v], fmi[1][v]));
+          h[v] = r.x + r.y;
         }
         T F[5];
         if (charwise) {
