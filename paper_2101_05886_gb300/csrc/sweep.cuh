@@ -195,6 +195,34 @@ __device__ __forceinline__ void dflux(T g1, T rinvB, const T uB[3], const T uA[3
   out[4] = (d[4] + dp) * UB + (EA + pA) * dU;
 }
 
+// dflux for two stencil points at once (same A state, two B states), packed.
+template <typename T>
+__device__ __forceinline__ void dflux_pair(T g1, typename PairOf<T>::type rinvB,
+                                           const typename PairOf<T>::type uB[3], const T uA[3],
+                                           const T mA[3], T EA, T pA,
+                                           const typename PairOf<T>::type d[5],
+                                           const typename PairOf<T>::type k[3],
+                                           typename PairOf<T>::type out[5]) {
+  using P = typename PairOf<T>::type;
+  const P du0 = pmul(pfma(pc<P>(-uA[0]), d[0], d[1]), rinvB);
+  const P du1 = pmul(pfma(pc<P>(-uA[1]), d[0], d[2]), rinvB);
+  const P du2 = pmul(pfma(pc<P>(-uA[2]), d[0], d[3]), rinvB);
+  P dke = pmul(d[1], uB[0]);
+  dke = pfma(d[2], uB[1], dke);
+  dke = pfma(d[3], uB[2], dke);
+  dke = pfma(pc<P>(mA[0]), du0, dke);
+  dke = pfma(pc<P>(mA[1]), du1, dke);
+  dke = pfma(pc<P>(mA[2]), du2, dke);
+  const P dp = pmul(pc<P>(g1), pfma(pc<P>(T(-0.5)), dke, d[4]));
+  const P UB = pfma(uB[2], k[2], pfma(uB[1], k[1], pmul(uB[0], k[0])));
+  const P dU = pfma(du2, k[2], pfma(du1, k[1], pmul(du0, k[0])));
+  out[0] = pfma(d[3], k[2], pfma(d[2], k[1], pmul(d[1], k[0])));
+  out[1] = pfma(dp, k[0], pfma(pc<P>(mA[0]), dU, pmul(d[1], UB)));
+  out[2] = pfma(dp, k[1], pfma(pc<P>(mA[1]), dU, pmul(d[2], UB)));
+  out[3] = pfma(dp, k[2], pfma(pc<P>(mA[2]), dU, pmul(d[3], UB)));
+  out[4] = pfma(pc<P>(EA + pA), dU, pmul(padd(d[4], dp), UB));
+}
+
 template <typename T, int M, int SCHEME>
 __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 ? 2 : 1))
 fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, int nitems, int dir,
@@ -503,20 +531,49 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 
         // split stencil values f+/- for m = i-2..i+3
         T fpl[6][5], fmi[6][5];
+        // f+- = (1/2) l.(dF +- lambda d (1/J)_m) of one stencil point
+        auto split_point = [&](int s, const T dF[5], const T d[5], T ijm) {
+          T cF[5], cD[5];
+          project(dF, cF);
+          project(d, cD);
+          const T mu0 = lam[0] * ijm, mu1 = lam[1] * ijm, mu4 = lam[4] * ijm;
+          const T mu[5] = {mu0, mu1, mu1, mu1, mu4};
 #pragma unroll
-        for (int s = 0; s < 6; ++s) {
-          const int q = s + 1;
-          // dF = F~ part, d = Q part before the 1/J of the point (folded into the speeds)
-          T dF[5], d[5];
-          const T km[3] = {CELL(CF_K, q), CELL(CF_K + 1, q), CELL(CF_K + 2, q)};
-          const T ijm = CELL(CF_INVJ, q);
-          const T uB[3] = {CELL(CF_U, q), CELL(CF_U + 1, q), CELL(CF_U + 2, q)};
-          if (fpform) {
+          for (int v = 0; v < 5; ++v) {
+            fpl[s][v] = cF[v] + mu[v] * cD[v];
+            fmi[s][v] = cF[v] - mu[v] * cD[v];
+          }
+        };
+        if (fpform) {
+          // reference-state differences of the stencil points two at a time (packed)
 #pragma unroll
-            for (int v = 0; v < 5; ++v) d[v] = (CELL(CF_Q + v, q) - Qi[v]) - dl[v];
-            dflux<T>(g1, CELL(CF_RINV, q), uB, us, ms, Qs[4], ps, d, km, dF);
-          } else {
-            // plain scheme: F~_m and Q~_m themselves
+          for (int s = 0; s < 6; s += 2) {
+            const int q = s + 1, q2 = s + 2;
+            P dp[5], kp2[3], uBp[3], out[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v)
+              dp[v] = psub(psub(pmk(CELL(CF_Q + v, q), CELL(CF_Q + v, q2)), pc<P>(Qi[v])), pc<P>(dl[v]));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              kp2[c] = pmk(CELL(CF_K + c, q), CELL(CF_K + c, q2));
+              uBp[c] = pmk(CELL(CF_U + c, q), CELL(CF_U + c, q2));
+            }
+            dflux_pair<T>(g1, pmk(CELL(CF_RINV, q), CELL(CF_RINV, q2)), uBp, us, ms, Qs[4], ps, dp, kp2, out);
+            const T dF0[5] = {out[0].x, out[1].x, out[2].x, out[3].x, out[4].x};
+            const T d0[5] = {dp[0].x, dp[1].x, dp[2].x, dp[3].x, dp[4].x};
+            split_point(s, dF0, d0, CELL(CF_INVJ, q));
+            const T dF1[5] = {out[0].y, out[1].y, out[2].y, out[3].y, out[4].y};
+            const T d1[5] = {dp[0].y, dp[1].y, dp[2].y, dp[3].y, dp[4].y};
+            split_point(s + 1, dF1, d1, CELL(CF_INVJ, q2));
+          }
+        } else {
+          // plain scheme: F~_m and Q~_m themselves
+#pragma unroll
+          for (int s = 0; s < 6; ++s) {
+            const int q = s + 1;
+            T dF[5], d[5];
+            const T km[3] = {CELL(CF_K, q), CELL(CF_K + 1, q), CELL(CF_K + 2, q)};
+            const T uB[3] = {CELL(CF_U, q), CELL(CF_U + 1, q), CELL(CF_U + 2, q)};
 #pragma unroll
             for (int v = 0; v < 5; ++v) d[v] = CELL(CF_Q + v, q);
             const T pm = g1 * (d[4] - T(0.5) * (d[1] * uB[0] + d[2] * uB[1] + d[3] * uB[2]));
@@ -526,17 +583,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
             dF[2] = d[2] * U + pm * km[1];
             dF[3] = d[3] * U + pm * km[2];
             dF[4] = (d[4] + pm) * U;
-          }
-          T cF[5], cD[5];
-          project(dF, cF);
-          project(d, cD);
-          // f+- = (1/2) l.(dF +- lambda d (1/J)_m)
-          const T mu0 = lam[0] * ijm, mu1 = lam[1] * ijm, mu4 = lam[4] * ijm;
-          const T mu[5] = {mu0, mu1, mu1, mu1, mu4};
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            fpl[s][v] = cF[v] + mu[v] * cD[v];
-            fmi[s][v] = cF[v] - mu[v] * cD[v];
+            split_point(s, dF, d, CELL(CF_INVJ, q));
           }
         }
 #undef CELL
