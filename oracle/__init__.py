@@ -52,6 +52,11 @@ def lib():
         L = ctypes.CDLL(_LIB_PATH)
         L.or_ghost.restype = ctypes.c_int
         L.or_node_ghost.restype = ctypes.c_int
+        L.or_ghost_s.restype = ctypes.c_int
+        L.or_node_ghost_s.restype = ctypes.c_int
+        L.or_weno7.argtypes = [_D]
+        L.or_weno7.restype = ctypes.c_double
+        L.or_weno7_parts.argtypes = [_D, _D, _D]
         L.or_interp_coef.argtypes = [ctypes.c_int, _D]
         L.or_weno5.argtypes = [_D]
         L.or_weno5.restype = ctypes.c_double
@@ -99,16 +104,16 @@ def cfg_for(grid, M=6, scheme=0, fp=1, charwise=1, form=2, gamma=1.4, qinf=None,
     return make_cfg(grid.dims, grid.n, M, scheme, fp, charwise, form, grid.bc, gamma, qinf, global_lf)
 
 
-def ghost(M: int) -> int:
-    return lib().or_ghost(M)
+def ghost(M: int, scheme: int = 0) -> int:
+    return lib().or_ghost_s(M, scheme)
 
 
-def node_ghost(M: int) -> int:
-    return lib().or_node_ghost(M)
+def node_ghost(M: int, scheme: int = 0) -> int:
+    return lib().or_node_ghost_s(M, scheme)
 
 
 def met_shape(cfg: Cfg):
-    G = ghost(cfg.M)
+    G = ghost(cfg.M, cfg.scheme)
     ni, nj, nk = cfg.n[0], cfg.n[1], cfg.n[2]
     if cfg.dims == 2:
         return (10, 1, nj + 2 * G, ni + 2 * G)
@@ -151,6 +156,19 @@ def cfl_dt(cfg: Cfg, met: np.ndarray, q: np.ndarray, cfl: float) -> float:
 def weno5(v) -> float:
     v = np.ascontiguousarray(v, dtype=np.float64)
     return lib().or_weno5(_p(v))
+
+
+def weno7(v) -> float:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return lib().or_weno7(_p(v))
+
+
+def weno7_parts(v):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    q = np.zeros(4)
+    b = np.zeros(4)
+    lib().or_weno7_parts(_p(v), _p(q), _p(b))
+    return q, b
 
 
 def lu5(v) -> float:

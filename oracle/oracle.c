@@ -37,6 +37,12 @@ static const double *interp_w(int M, double *den) {
 
 int or_ghost(int M) { return M / 2 > 3 ? M / 2 : 3; }
 int or_node_ghost(int M) { return or_ghost(M) + 3 * (M / 2); }
+/* the 7th-order stencil reaches four points past a face */
+int or_ghost_s(int M, int scheme) {
+  int r = scheme == 2 ? 4 : 3;
+  return M / 2 > r ? M / 2 : r;
+}
+int or_node_ghost_s(int M, int scheme) { return or_ghost_s(M, scheme) + 3 * (M / 2); }
 
 void or_interp_coef(int M, double c[8]) {
   double den;
@@ -141,6 +147,7 @@ static int valid_cfg(const or_cfg *c) {
   if (!c) return 0;
   if (c->dims != 2 && c->dims != 3) return 0;
   if (c->M != 2 && c->M != 4 && c->M != 6 && c->M != 8) return 0;
+  if (c->scheme < 0 || c->scheme > 2) return 0;
   for (int d = 0; d < 3; ++d) if (c->n[d] < 1) return 0;
   if (c->dims == 2 && c->n[2] != 1) return 0;
   return 1;
@@ -148,7 +155,7 @@ static int valid_cfg(const or_cfg *c) {
 
 int or_metrics(const or_cfg *c, const double *nodes, int Gn, double *met) {
   if (!valid_cfg(c) || !nodes || !met) return 1;
-  const int M = c->M, h = M / 2, G = or_ghost(M), D = c->dims;
+  const int M = c->M, h = M / 2, G = or_ghost_s(M, c->scheme), D = c->dims;
   if (Gn < G + 3 * h) return 1;
   int nlo[3], nhi[3], b1lo[3], b1hi[3], b2lo[3], b2hi[3], b3lo[3], b3hi[3];
   for (int d = 0; d < 3; ++d) {
@@ -289,6 +296,46 @@ double or_weno5(const double v[5]) {
   return r;
 }
 
+/* Standard 7th-order WENO (cited in Sec. 4; Remark 2 extends the FP form to it), from
+   the general WENO construction: four 4-point sub-stencils, face values q_k of the
+   cubic reconstructions, smoothness indicators from the integral definition
+   beta_k = sum_{l=1..3} int_{cell} h^(2l-1) (p_k^(l))^2 (the quadratic forms below are
+   240 beta_k), optimal weights (1, 12, 18, 4)/35, eps = 1e-6, power 2. */
+void or_weno7_parts(const double v[7], double q[4], double beta[4]) {
+  q[0] = (-3.0 * v[0] + 13.0 * v[1] - 23.0 * v[2] + 25.0 * v[3]) / 12.0;
+  q[1] = (v[1] - 5.0 * v[2] + 13.0 * v[3] + 3.0 * v[4]) / 12.0;
+  q[2] = (-v[2] + 7.0 * v[3] + 7.0 * v[4] - v[5]) / 12.0;
+  q[3] = (3.0 * v[3] + 13.0 * v[4] - 5.0 * v[5] + v[6]) / 12.0;
+  const double *a = v;
+  beta[0] = (a[0] * (547.0 * a[0] - 3882.0 * a[1] + 4642.0 * a[2] - 1854.0 * a[3]) +
+             a[1] * (7043.0 * a[1] - 17246.0 * a[2] + 7042.0 * a[3]) +
+             a[2] * (11003.0 * a[2] - 9402.0 * a[3]) + 2107.0 * a[3] * a[3]) / 240.0;
+  beta[1] = (a[1] * (267.0 * a[1] - 1642.0 * a[2] + 1602.0 * a[3] - 494.0 * a[4]) +
+             a[2] * (2843.0 * a[2] - 5966.0 * a[3] + 1922.0 * a[4]) +
+             a[3] * (3443.0 * a[3] - 2522.0 * a[4]) + 547.0 * a[4] * a[4]) / 240.0;
+  beta[2] = (a[2] * (547.0 * a[2] - 2522.0 * a[3] + 1922.0 * a[4] - 494.0 * a[5]) +
+             a[3] * (3443.0 * a[3] - 5966.0 * a[4] + 1602.0 * a[5]) +
+             a[4] * (2843.0 * a[4] - 1642.0 * a[5]) + 267.0 * a[5] * a[5]) / 240.0;
+  beta[3] = (a[3] * (2107.0 * a[3] - 9402.0 * a[4] + 7042.0 * a[5] - 1854.0 * a[6]) +
+             a[4] * (11003.0 * a[4] - 17246.0 * a[5] + 4642.0 * a[6]) +
+             a[5] * (7043.0 * a[5] - 3882.0 * a[6]) + 547.0 * a[6] * a[6]) / 240.0;
+}
+
+double or_weno7(const double v[7]) {
+  static const double C7[4] = {1.0 / 35.0, 12.0 / 35.0, 18.0 / 35.0, 4.0 / 35.0};
+  const double eps = 1.0e-6;
+  double q[4], beta[4], alpha[4], s = 0.0;
+  or_weno7_parts(v, q, beta);
+  for (int k = 0; k < 4; ++k) {
+    double t = beta[k] + eps;
+    alpha[k] = C7[k] / (t * t);
+    s += alpha[k];
+  }
+  double r = 0.0;
+  for (int k = 0; k < 4; ++k) r += (alpha[k] / s) * q[k];
+  return r;
+}
+
 /* Appendix, Eq. (new_form_linear_upwind): the linear upwind scheme is WENO with
    the optimal weights C_k, which reproduces Eq. (linear_upwind). */
 double or_lu5(const double v[5]) {
@@ -421,10 +468,11 @@ static void face_flux_impl(const or_cfg *c, const double q8[40], const double me
     Qtf[v] = interp_face(M, fw);
     Qs[v] = Qtf[v] / invJf;             /* Eq. (Q_star) */
   }
-  /* stencil values m = i-2..i+3 (window positions 1..6) */
-  double gF[6][5], gQ[6][5];
-  for (int s = 0; s < 6; ++s) {
-    int m = s + 1;
+  /* stencil values m = i-2..i+3 (window positions 1..6), i-3..i+4 for WENO7 (0..7) */
+  const int ns = c->scheme == 2 ? 8 : 6, m0 = c->scheme == 2 ? 0 : 1;
+  double gF[8][5], gQ[8][5];
+  for (int s = 0; s < ns; ++s) {
+    int m = s + m0;
     const double *Qm = q8 + m * 5;
     double km[3] = {met8[m * 4 + 0], met8[m * 4 + 1], met8[m * 4 + 2]};
     double Ft[5];
@@ -463,8 +511,8 @@ static void face_flux_impl(const or_cfg *c, const double q8[40], const double me
   double lam[5] = {0, 0, 0, 0, 0};
   if (lam_given)
     for (int v = 0; v < 5; ++v) lam[v] = lam_given[v];
-  for (int s = 0; s < 6 && !lam_given; ++s) {
-    int m = s + 1;
+  for (int s = 0; s < ns && !lam_given; ++s) {
+    int m = s + m0;
     double km[3] = {met8[m * 4 + 0], met8[m * 4 + 1], met8[m * 4 + 2]};
     double e[5];
     point_eigs(q8 + m * 5, km, invJ[m], gamma, e);
@@ -478,17 +526,25 @@ static void face_flux_impl(const or_cfg *c, const double q8[40], const double me
   /* characteristic Lax-Friedrichs splitting and reconstruction per field */
   double h[5];
   for (int sf = 0; sf < 5; ++sf) {
-    double fpl[6], fmi[6];
-    for (int s = 0; s < 6; ++s) {
+    double fpl[8], fmi[8];
+    for (int s = 0; s < ns; ++s) {
       double a = 0.0, b = 0.0;
       for (int v = 0; v < 5; ++v) { a += Lm[sf * 5 + v] * gF[s][v]; b += Lm[sf * 5 + v] * gQ[s][v]; }
       fpl[s] = 0.5 * (a + lam[sf] * b);
       fmi[s] = 0.5 * (a - lam[sf] * b);
     }
-    double vp[5] = {fpl[0], fpl[1], fpl[2], fpl[3], fpl[4]};        /* i-2 .. i+2 */
-    double vm[5] = {fmi[5], fmi[4], fmi[3], fmi[2], fmi[1]};        /* i+3 .. i-1 */
-    double rp = c->scheme == 1 ? or_lu5(vp) : or_weno5(vp);
-    double rm = c->scheme == 1 ? or_lu5(vm) : or_weno5(vm);
+    double rp, rm;
+    if (c->scheme == 2) {
+      double vp[7], vm[7];
+      for (int t = 0; t < 7; ++t) { vp[t] = fpl[t]; vm[t] = fmi[7 - t]; }   /* i-3..i+3 and i+4..i-2 */
+      rp = or_weno7(vp);
+      rm = or_weno7(vm);
+    } else {
+      double vp[5] = {fpl[0], fpl[1], fpl[2], fpl[3], fpl[4]};        /* i-2 .. i+2 */
+      double vm[5] = {fmi[5], fmi[4], fmi[3], fmi[2], fmi[1]};        /* i+3 .. i-1 */
+      rp = c->scheme == 1 ? or_lu5(vp) : or_weno5(vp);
+      rm = c->scheme == 1 ? or_lu5(vm) : or_weno5(vm);
+    }
     h[sf] = rp + rm;
   }
   for (int v = 0; v < 5; ++v) {
@@ -545,7 +601,7 @@ static double *ghost_state(const or_cfg *c, const double *q, int G, int lo[3], i
 
 int or_rhs(const or_cfg *c, const double *met, const double *q, double *R, double *dqdt) {
   if (!valid_cfg(c) || !met || !q) return 1;
-  const int G = or_ghost(c->M);
+  const int G = or_ghost_s(c->M, c->scheme);
   for (int d = 0; d < c->dims; ++d) if (c->n[d] < G) return 1;
   int lo[3], hi[3];
   double *g = ghost_state(c, q, G, lo, hi);
@@ -642,7 +698,7 @@ int or_rk3_step(const or_cfg *c, const double *met, double *q, double dt) {
 
 /* dt = CFL / max over points of sum_d (|U_d| + c |grad d|), grad d = J k_d. */
 double or_cfl_dt(const or_cfg *c, const double *met, const double *q, double cfl) {
-  const int G = or_ghost(c->M), ni = c->n[0], nj = c->n[1], nk = c->n[2];
+  const int G = or_ghost_s(c->M, c->scheme), ni = c->n[0], nj = c->n[1], nk = c->n[2];
   int lo[3], hi[3];
   for (int d = 0; d < 3; ++d) {
     int on = d < c->dims;

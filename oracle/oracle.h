@@ -27,7 +27,7 @@ typedef struct {
   int dims;        /* 2 or 3 */
   int n[3];        /* ni, nj, nk (nk = 1 in 2-D) */
   int M;           /* metric and face-interpolation order: 2, 4, 6 or 8 */
-  int scheme;      /* 0 = WENO5-JS, 1 = 5th-order linear upwind */
+  int scheme;      /* 0 = WENO5-JS, 1 = 5th-order linear upwind, 2 = WENO7-JS */
   int fp;          /* 1 = free-stream-preserving form, 0 = plain scheme */
   int charwise;    /* 1 = characteristic-wise (Roe eigenvectors), 0 = component-wise */
   int form;        /* 2 = WENO(F_m - F*_m + F*_face) (Eq. my_point2), 1 = WENO(F_m - F*_m) + F*_face (Eq. my_point1) */
@@ -37,11 +37,15 @@ typedef struct {
   double qinf[5];
 } or_cfg;
 
-int or_ghost(int M);                 /* G = max(3, M/2) */
+int or_ghost(int M);                 /* G = max(3, M/2) for the 5th-order schemes */
 int or_node_ghost(int M);            /* G + 3M/2 */
+int or_ghost_s(int M, int scheme);   /* G = max(3 or 4 (WENO7), M/2) */
+int or_node_ghost_s(int M, int scheme);
 void or_interp_coef(int M, double c[8]);      /* face interpolation weights (Sec. 3) */
 double or_weno5(const double v[5]);           /* WENO5-JS of v[0..4] = f_{i-2..i+2} at i+1/2 */
 double or_lu5(const double v[5]);             /* linear upwind 5 = WENO with optimal weights */
+double or_weno7(const double v[7]);           /* WENO7-JS of v[0..6] = f_{i-3..i+3} at i+1/2 */
+void or_weno7_parts(const double v[7], double q[4], double beta[4]);
 void or_eigensystem(const double qL[5], const double qR[5], const double k[3], double gamma,
                     double L[25], double R[25]);
 int or_metrics(const or_cfg *c, const double *nodes, int Gn, double *met);

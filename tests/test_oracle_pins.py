@@ -566,3 +566,114 @@ def test_global_speeds_enter_the_dissipation_linearly():
     f1 = O.face_flux_lam(cfg, q8, met8, lam)
     f2 = O.face_flux_lam(cfg, q8, met8, 2 * lam)
     assert np.abs((f2 - central) - 2 * (f1 - central)).max() < 1e-12 * np.abs(central).max()
+
+
+# ---------------------------------------------------------------- WENO7 (Remark 2)
+def test_weno7_optimal_weights_give_the_7th_order_upwind_stencil():
+    C = np.array([1, 12, 18, 4]) / 35.0
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        v = rng.standard_normal(7)
+        q, _ = O.weno7_parts(v)
+        ref = (-3 * v[0] + 25 * v[1] - 101 * v[2] + 319 * v[3] + 214 * v[4] - 38 * v[5] + 4 * v[6]) / 420.0
+        assert abs(C @ q - ref) < 1e-14 * (1 + np.abs(v).sum())
+
+
+def test_weno7_smoothness_indicators_follow_the_integral_definition():
+    """beta_k = sum_{l=1..3} int_{-1/2}^{1/2} (p_k^(l))^2 dx for the cubic p_k whose cell
+    averages over the sub-stencil are the data (h = 1)."""
+    rng = np.random.default_rng(4)
+    v = rng.standard_normal(7)
+    _, beta = O.weno7_parts(v)
+    for k in range(4):
+        cells = np.arange(k - 3, k + 1)
+        # cell average of x^j over [c - 1/2, c + 1/2]
+        A = np.array([[((c + 0.5) ** (j + 1) - (c - 0.5) ** (j + 1)) / (j + 1) for j in range(4)] for c in cells])
+        a = np.linalg.solve(A, v[cells + 3])
+        p = np.polynomial.Polynomial(a)
+        b = 0.0
+        for l in range(1, 4):
+            dl = p.deriv(l) ** 2
+            it = dl.integ()
+            b += it(0.5) - it(-0.5)
+        assert abs(b - beta[k]) < 1e-10 * (1 + abs(b))
+
+
+def test_weno7_seventh_order_and_non_oscillatory():
+    errs = []
+    for n in (32, 64):
+        h = 2 * np.pi / n
+        x = np.arange(n) * h
+        cellavg = (np.cos(x - h / 2) - np.cos(x + h / 2)) / h
+        e = 0.0
+        for i in range(3, n - 3):
+            e = max(e, abs(O.weno7(cellavg[i - 3:i + 4]) - np.sin(x[i] + h / 2)))
+        errs.append(e)
+    assert np.log2(errs[0] / errs[1]) > 6.0
+    assert abs(O.weno7([0, 0, 0, 0, 1, 1, 1])) < 1e-9
+
+
+def test_table1_weno7_rows():
+    rows = {r[0]: [float(x) for x in r[1:]] for r in read_golden("table1_free_stream.txt")}
+    qinf = I.uniform_qinf(0.5, 0.0)
+    for M, fp, key in ((6, 1, "WENO7-M6"), (8, 1, "WENO7-M8"), (6, 0, "WENO7")):
+        Gn = O.node_ghost(M, 2)
+        g = I.paper_wavy_2d(Gn=Gn)
+        cfg = O.cfg_for(g, M=M, scheme=2, fp=fp, qinf=qinf)
+        met = O.metrics(cfg, g.nodes, Gn)
+        q = I.uniform_state(g, qinf)
+        for _ in range(100):
+            q = O.rk3_step(cfg, met, q, 0.2)
+        v = q[2] / q[0]
+        l2 = np.sqrt(np.mean(v * v))
+        paper = rows[key][0]
+        if fp:
+            assert l2 < 10 * paper
+        else:
+            assert paper / 10 < l2 < paper * 10
+
+
+def test_table2_weno7_m8_at_21_and_41_points():
+    ref = {(r[0], int(r[1])): float(r[2]) for r in read_golden("table2_vortex.txt")}
+    qinf = I.uniform_qinf(0.5, 0.0)
+    M = 8
+    Gn = O.node_ghost(M, 2)
+    for npts, dt in ((21, 0.1), (41, 0.05)):
+        g = I.paper_wavy_2d(npts=npts, Gn=Gn)
+        x, y = g.interior_xyz()
+        q = I.paper_vortex(x, y, 0.0)
+        cfg = O.cfg_for(g, M=M, scheme=2, qinf=qinf)
+        met = O.metrics(cfg, g.nodes, Gn)
+        for _ in range(int(round(40.0 / dt))):
+            q = O.rk3_step(cfg, met, q, dt)
+        qe = I.paper_vortex(x, y, 40.0)
+        e2 = np.sqrt(np.mean((q[2] / q[0] - qe[2] / qe[0]) ** 2))
+        p2 = ref[("WENO7-M8", npts)]
+        assert p2 / 1.3 < e2 < p2 * 1.3, (npts, e2, p2)
+
+
+def test_weno7_m8_design_order_on_the_vortex():
+    errs = []
+    for n in (64, 128):
+        Gn = O.node_ghost(8, 2)
+        g = I.periodic_wavy_2d(n, L=10.0, amp=0.1, Gn=Gn)
+        x, y = g.interior_xyz()
+        q = I.shu_vortex(x, y, 0.0, 5.0, 5.0, eps=5.0, mach=0.5, L=10.0)
+        cfg = O.cfg_for(g, M=8, scheme=2)
+        L = O.rhs(cfg, O.metrics(cfg, g.nodes, Gn), q)[1]
+        exact = -0.5 * np.sqrt(GAMMA) * np.imag(_vortex_complex(x + 1e-30j, y)) / 1e-30
+        core = ((x - 5) ** 2 + (y - 5) ** 2 < 3.5 ** 2)[None]
+        errs.append(np.abs((L - exact) * core).max())
+    assert np.log2(errs[0] / errs[1]) > 6.5
+
+
+@pytest.mark.parametrize("M", [4, 8])
+def test_remark1_weno7_bitwise_on_cartesian_grid(M):
+    Gn = O.node_ghost(M, 2)
+    g = I.cartesian_3d((9, 8, 10), 0.125, Gn)
+    q = I.random_smooth_state(g, I.uniform_qinf(0.7, 25.0, 10.0), amp=0.1, seed=3)
+    R = {}
+    for fp in (1, 0):
+        cfg = O.cfg_for(g, M=M, scheme=2, fp=fp)
+        R[fp] = O.rhs(cfg, O.metrics(cfg, g.nodes, Gn), q)[0]
+    assert np.array_equal(R[1], R[0])
