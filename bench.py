@@ -137,7 +137,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     M = 6
-    Gn = B.fp_node_ghost_width(M)
+    Gn = B.fp_node_ghost_width(M, B.FP_WENO5_JS)
     qinf = I.uniform_qinf(3.0, 0.0)
     prec = B.FP_F32_MIXED
     sizes = I.batched_block_sizes(64, 32, 128, 4)[:args.blocks]
@@ -291,14 +291,16 @@ def run_gpu(args):
 
 def run_variants(I, B, Block, Gn, M, torch, stream, nsteps=5):
     """FP32 RK3 steps on one 256^3 wavy block (Mach 0.8 + vortex) for the paper's
-    characteristic WENO5-JS, the linear-upwind scheme and component-wise WENO5-JS."""
+    characteristic WENO5-JS, the linear-upwind scheme, component-wise WENO5-JS and
+    characteristic WENO7-JS (all under the free-stream-preserving form, metric order M)."""
+    Gn = max(Gn, B.fp_node_ghost_width(M, B.FP_WENO7_JS))
     g = I.periodic_wavy_3d((256, 256, 256), L=10.0, amp=0.08, Gn=Gn)
     qinf = I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0)
     q0 = I.vortex_3d(g, mach=0.8, eps=5.0, L=10.0)
     ncell = 256 ** 3
     out = {}
     for name, scheme, charw in (("weno5_char", B.FP_WENO5_JS, 1), ("lu5_char", B.FP_LINEAR_UPWIND5, 1),
-                                ("weno5_comp", B.FP_WENO5_JS, 0)):
+                                ("weno5_comp", B.FP_WENO5_JS, 0), ("weno7_char", B.FP_WENO7_JS, 1)):
         blk = Block(g, metric_order=M, scheme=scheme, characteristic=charw, precision=B.FP_F32_MIXED,
                     q_inf=qinf)
         q = blk.to_device(q0)

@@ -47,7 +47,8 @@ typedef enum {
   FP_ERR_UNSUPPORTED = 6   /* valid but not implemented combination */
 } fp_status;
 
-enum { FP_WENO5_JS = 0, FP_LINEAR_UPWIND5 = 1 };            /* reconstruction, Sec. 2.2.2 */
+enum { FP_WENO5_JS = 0, FP_LINEAR_UPWIND5 = 1, FP_WENO7_JS = 2 };  /* reconstruction: Sec. 2.2.2;
+                                                                    WENO7 per Remark 2 */
 enum { FP_F64 = 0, FP_F32_MIXED = 1 };                      /* precision of the sweep */
 enum { FP_BC_PERIODIC = 0, FP_BC_FARFIELD = 1, FP_BC_EXTRAP = 2 };
 enum { FP_XI = 0, FP_ETA = 1, FP_ZETA = 2 };
@@ -57,14 +58,14 @@ typedef struct {
   int n[3];                   /* solution points ni, nj, nk (nk = 1 when dims == 2) */
   int metric_order;           /* M in {2,4,6,8}: order of metrics, Jacobian and every
                                  face interpolation (Sec. 3 Eq. metric_discret, Remark 3) */
-  int scheme;                 /* FP_WENO5_JS or FP_LINEAR_UPWIND5 */
+  int scheme;                 /* FP_WENO5_JS, FP_LINEAR_UPWIND5 or FP_WENO7_JS */
   int free_stream_preserving; /* 1 = the paper's FP face flux, 0 = plain scheme (control) */
   int characteristic;         /* 1 = Roe characteristic-wise splitting (paper), 0 = component-wise */
   int precision;              /* FP_F64, or FP_F32_MIXED: metrics built in FP64, sweep in FP32 */
   int bc[3][2];               /* per direction (lo, hi): FP_BC_PERIODIC | FP_BC_FARFIELD | FP_BC_EXTRAP */
   double gamma;               /* ratio of specific heats (Sec. 2.1 Eq. EOS: 1.4) */
   double q_inf[5];            /* far-field state; also the reference state of the FP32 form */
-  int global_lf;              /* 0 = local Lax-Friedrichs speeds (max over the 6-point stencil),
+  int global_lf;              /* 0 = local Lax-Friedrichs speeds (max over the face's stencil),
                                  1 = global speeds (max over the block, per direction and
                                  characteristic field, refreshed every RK stage); Sec. 4 uses
                                  global splitting for its shock cases */
@@ -73,19 +74,20 @@ typedef struct {
 typedef struct fp_ctx fp_ctx;
 typedef struct fp_batch fp_batch;
 
-/* Ghost width G = max(3, M/2) of the stored metrics. */
-int fp_ghost_width(int metric_order);
+/* Ghost width G of the stored metrics: max(3, M/2), or max(4, M/2) for WENO7 (the
+   stencil reach past a face versus the order-M face interpolation). */
+int fp_ghost_width(int metric_order, int scheme);
 /* Node ghost layers required by fp_init_grid: G + 3M/2 (the metric products,
    the metrics and the Jacobian are all formed by the same order-M central
    operator, so every cell a stencil can reach satisfies the discrete surface
    conservation law, Sec. 2.1 Eq. SCL). */
-int fp_node_ghost_width(int metric_order);
+int fp_node_ghost_width(int metric_order, int scheme);
 
 /* Build a block: copies the node coordinates to the device and forms, in FP64,
    the symmetric conservative metrics (Eq. JBabc), the Jacobian (Eq. JB), the
    face metrics of every direction (Eq. xidJ at order M) and the work lists.
    xyz_nodes_host: double [dims][nk+2g][nj+2g][ni+2g] (2-D: [2][nj+2g][ni+2g]),
-   g = ghost_nodes >= fp_node_ghost_width(M); read during the call only.
+   g = ghost_nodes >= fp_node_ghost_width(M, scheme); read during the call only.
    Allocates device memory owned by the context.  Synchronises `stream`. */
 int fp_init_grid(const fp_grid_desc *desc, const double *xyz_nodes_host, int ghost_nodes,
                  void *stream, fp_ctx **out);
@@ -105,7 +107,7 @@ int fp_rk3_step(fp_ctx *ctx, void *q_dev, double dt, void *stream);
    Synchronises `stream` to return the value in *dt_out (host). */
 int fp_cfl_dt(fp_ctx *ctx, const void *q_dev, double cfl, double *dt_out, void *stream);
 
-/* Copy the stored cell metrics to host memory: double [10][nk+2G][nj+2G][ni+2G]
+/* Copy the stored cell metrics to host memory: double [10][nk+2G][nj+2G][ni+2G], G = fp_ghost_width
    (2-D: [10][1][nj+2G][ni+2G]); entry 3d+a is (d-th coordinate)_{x_a}/J, entry 9
    is 1/J.  Values are those the sweep uses (rounded to float for FP_F32_MIXED). */
 int fp_get_metrics(fp_ctx *ctx, double *host_out);

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfpgb300.so")
 
 FP_OK, FP_ERR_ARG, FP_ERR_CUDA, FP_ERR_OOM, FP_ERR_NONFINITE, FP_ERR_TIMEOUT, FP_ERR_UNSUPPORTED = range(7)
-FP_WENO5_JS, FP_LINEAR_UPWIND5 = 0, 1
+FP_WENO5_JS, FP_LINEAR_UPWIND5, FP_WENO7_JS = 0, 1, 2
 FP_F64, FP_F32_MIXED = 0, 1
 FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP = 0, 1, 2
 
@@ -47,8 +47,8 @@ def lib():
         if not os.path.exists(LIB_PATH):
             raise OSError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
         L = ctypes.CDLL(LIB_PATH)
-        L.fp_ghost_width.argtypes = [ctypes.c_int]
-        L.fp_node_ghost_width.argtypes = [ctypes.c_int]
+        L.fp_ghost_width.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.fp_node_ghost_width.argtypes = [ctypes.c_int, ctypes.c_int]
         L.fp_init_grid.argtypes = [ctypes.POINTER(fp_grid_desc), _VP, ctypes.c_int, _VP, ctypes.POINTER(_VP)]
         L.fp_rhs.argtypes = [_VP, _VP, _VP, _VP]
         L.fp_rhs_noalloc.argtypes = [_VP, _VP, _VP, _VP]
@@ -117,12 +117,12 @@ def make_desc(dims, n, metric_order=6, scheme=FP_WENO5_JS, fp=1, characteristic=
     return d
 
 
-def fp_ghost_width(M):
-    return lib().fp_ghost_width(M)
+def fp_ghost_width(M, scheme=FP_WENO5_JS):
+    return lib().fp_ghost_width(M, scheme)
 
 
-def fp_node_ghost_width(M):
-    return lib().fp_node_ghost_width(M)
+def fp_node_ghost_width(M, scheme=FP_WENO5_JS):
+    return lib().fp_node_ghost_width(M, scheme)
 
 
 def fp_init_grid(desc, nodes_host_ptr, ghost_nodes, stream=0):

@@ -80,7 +80,8 @@ int bfail(fp_batch *b, int st, const std::string &msg) {
   return st;
 }
 
-int ghost_of(int M) { return std::max(3, M / 2); }
+// ghost width: the stencil reach past a face (3, or 4 for WENO7) or the face interpolation's M/2
+int ghost_of(int M, int scheme) { return std::max(scheme == FP_WENO7_JS ? 4 : 3, M / 2); }
 
 int prepare(int is_f32, int M, int scheme) {
   return is_f32 ? fpk::prepare_sweep_f32(M, scheme) : fpk::prepare_sweep_f64(M, scheme);
@@ -195,7 +196,8 @@ int validate(const fp_grid_desc *d, int ghost_nodes, std::string &why) {
   if (d->dims != 2 && d->dims != 3) { why = "dims must be 2 or 3"; return 0; }
   const int M = d->metric_order;
   if (M != 2 && M != 4 && M != 6 && M != 8) { why = "metric_order must be 2, 4, 6 or 8"; return 0; }
-  const int G = ghost_of(M);
+  if (d->scheme != FP_WENO5_JS && d->scheme != FP_LINEAR_UPWIND5 && d->scheme != FP_WENO7_JS) { why = "unknown scheme"; return 0; }
+  const int G = ghost_of(M, d->scheme);
   for (int k = 0; k < 3; ++k) {
     if (d->n[k] < 1) { why = "n must be positive"; return 0; }
     if (k < d->dims && d->n[k] < G) { why = "each swept extent must be at least the ghost width"; return 0; }
@@ -203,7 +205,6 @@ int validate(const fp_grid_desc *d, int ghost_nodes, std::string &why) {
   }
   if (d->dims == 2 && d->n[2] != 1) { why = "n[2] must be 1 in 2-D"; return 0; }
   if ((long long)d->n[0] * d->n[1] * d->n[2] > (1LL << 31) - 1) { why = "too many points"; return 0; }
-  if (d->scheme != FP_WENO5_JS && d->scheme != FP_LINEAR_UPWIND5) { why = "unknown scheme"; return 0; }
   if (d->precision != FP_F64 && d->precision != FP_F32_MIXED) { why = "unknown precision"; return 0; }
   if (d->free_stream_preserving != 0 && d->free_stream_preserving != 1) { why = "free_stream_preserving must be 0 or 1"; return 0; }
   if (d->characteristic != 0 && d->characteristic != 1) { why = "characteristic must be 0 or 1"; return 0; }
@@ -216,7 +217,7 @@ int validate(const fp_grid_desc *d, int ghost_nodes, std::string &why) {
   if (!(rho > 0.0)) { why = "q_inf density must be positive"; return 0; }
   double ke = 0.5 * (d->q_inf[1] * d->q_inf[1] + d->q_inf[2] * d->q_inf[2] + d->q_inf[3] * d->q_inf[3]) / rho;
   if (!((d->gamma - 1.0) * (d->q_inf[4] - ke) > 0.0)) { why = "q_inf pressure must be positive"; return 0; }
-  if (ghost_nodes < G + 3 * (M / 2)) { why = "ghost_nodes below fp_node_ghost_width(metric_order)"; return 0; }
+  if (ghost_nodes < G + 3 * (M / 2)) { why = "ghost_nodes below fp_node_ghost_width(metric_order, scheme)"; return 0; }
   return 1;
 }
 
@@ -224,8 +225,10 @@ int validate(const fp_grid_desc *d, int ghost_nodes, std::string &why) {
 
 extern "C" {
 
-int fp_ghost_width(int metric_order) { return ghost_of(metric_order); }
-int fp_node_ghost_width(int metric_order) { return ghost_of(metric_order) + 3 * (metric_order / 2); }
+int fp_ghost_width(int metric_order, int scheme) { return ghost_of(metric_order, scheme); }
+int fp_node_ghost_width(int metric_order, int scheme) {
+  return ghost_of(metric_order, scheme) + 3 * (metric_order / 2);
+}
 
 const char *fp_status_string(int st) {
   switch (st) {
@@ -265,7 +268,7 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
   std::memset(&c->uploaded, 0xff, sizeof(BlockDev));
   c->desc = *desc;
   const int dims = desc->dims, M = desc->metric_order;
-  c->G = ghost_of(M);
+  c->G = ghost_of(M, desc->scheme);
   c->is_f32 = desc->precision == FP_F32_MIXED;
   c->esize = c->is_f32 ? sizeof(float) : sizeof(double);
   const int *n = desc->n;

@@ -112,6 +112,40 @@ __device__ __forceinline__ typename PairOf<T>::type recon5_pair(
   return pfma(num, pmk(Num<T>::rcp(den.x), Num<T>::rcp(den.y)), v2);
 }
 
+// Seventh-order WENO-JS (four 4-point sub-stencils, optimal weights (1,12,18,4)/35,
+// smoothness indicators of the integral definition) for a pair of seven-point stencils,
+// written in the first differences d1..d6 of the seven values.
+template <typename T>
+__device__ __forceinline__ typename PairOf<T>::type recon7_pair(const typename PairOf<T>::type v[7]) {
+  using P = typename PairOf<T>::type;
+  const P d1 = psub(v[1], v[0]), d2 = psub(v[2], v[1]), d3 = psub(v[3], v[2]);
+  const P d4 = psub(v[4], v[3]), d5 = psub(v[5], v[4]), d6 = psub(v[6], v[5]);
+  // 12 (q_k - v3)
+  const P r0 = pfma(pc<P>(T(13)), d3, pfma(pc<P>(T(-10)), d2, pmul(pc<P>(T(3)), d1)));
+  const P r1 = pfma(pc<P>(T(3)), d4, pfma(pc<P>(T(4)), d3, pmul(pc<P>(T(-1)), d2)));
+  const P r2 = pfma(pc<P>(T(-1)), d5, pfma(pc<P>(T(6)), d4, d3));
+  const P r3 = pfma(pc<P>(T(9)), d4, pfma(pc<P>(T(-4)), d5, d6));
+  // 240 beta_k as quadratic forms of the differences
+  const P f0 = pfma(d1, pfma(pc<P>(T(547)), d1, pfma(pc<P>(T(-2788)), d2, pmul(pc<P>(T(1854)), d3))),
+                    pfma(d2, pfma(pc<P>(T(3708)), d2, pmul(pc<P>(T(-5188)), d3)), pmul(pc<P>(T(2107)), pmul(d3, d3))));
+  const P f1 = pfma(d2, pfma(pc<P>(T(267)), d2, pfma(pc<P>(T(-1108)), d3, pmul(pc<P>(T(494)), d4))),
+                    pfma(d3, pfma(pc<P>(T(1468)), d3, pmul(pc<P>(T(-1428)), d4)), pmul(pc<P>(T(547)), pmul(d4, d4))));
+  const P f2 = pfma(d3, pfma(pc<P>(T(547)), d3, pfma(pc<P>(T(-1428)), d4, pmul(pc<P>(T(494)), d5))),
+                    pfma(d4, pfma(pc<P>(T(1468)), d4, pmul(pc<P>(T(-1108)), d5)), pmul(pc<P>(T(267)), pmul(d5, d5))));
+  const P f3 = pfma(d4, pfma(pc<P>(T(2107)), d4, pfma(pc<P>(T(-5188)), d5, pmul(pc<P>(T(1854)), d6))),
+                    pfma(d5, pfma(pc<P>(T(3708)), d5, pmul(pc<P>(T(-2788)), d6)), pmul(pc<P>(T(547)), pmul(d6, d6))));
+  const P i240 = pc<P>(T(1.0 / 240.0)), eps = pc<P>(T(1.0e-6));
+  const P b0 = pfma(f0, i240, eps), b1 = pfma(f1, i240, eps), b2 = pfma(f2, i240, eps), b3 = pfma(f3, i240, eps);
+  const P s0 = pmul(b0, b0), s1 = pmul(b1, b1), s2 = pmul(b2, b2), s3 = pmul(b3, b3);
+  const P a0 = pmul(pc<P>(T(1.0 / 35.0)), pmk(Num<T>::rcp(s0.x), Num<T>::rcp(s0.y)));
+  const P a1 = pmul(pc<P>(T(12.0 / 35.0)), pmk(Num<T>::rcp(s1.x), Num<T>::rcp(s1.y)));
+  const P a2 = pmul(pc<P>(T(18.0 / 35.0)), pmk(Num<T>::rcp(s2.x), Num<T>::rcp(s2.y)));
+  const P a3 = pmul(pc<P>(T(4.0 / 35.0)), pmk(Num<T>::rcp(s3.x), Num<T>::rcp(s3.y)));
+  const P num = pfma(a3, r3, pfma(a2, r2, pfma(a1, r1, pmul(a0, r0))));
+  const P den = pmul(pc<P>(T(12)), padd(padd(a0, a1), padd(a2, a3)));
+  return pfma(num, pmk(Num<T>::rcp(den.x), Num<T>::rcp(den.y)), v[3]);
+}
+
 // Asynchronous global -> shared copies of single elements (sm_80+ cp.async).
 template <typename T>
 __device__ __forceinline__ void cp_async_el(T *smem, const T *gmem) {
@@ -224,9 +258,12 @@ __device__ __forceinline__ void dflux_pair(T g1, typename PairOf<T>::type rinvB,
 }
 
 template <typename T, int M, int SCHEME>
-__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 ? 2 : 1))
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && SCHEME != 2 ? 2 : 1))
 fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, int nitems, int dir,
          int mode, int stage, const double *__restrict__ dtp, int charwise, int fpform) {
+  // stencil points of a face: i-2..i+3 (5th order) or i-3..i+4 (WENO7), offset index Q0
+  constexpr int NS = SCHEME == 2 ? 8 : 6;
+  constexpr int Q0 = SCHEME == 2 ? 0 : 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   T *const sm = reinterpret_cast<T *>(smraw);              // cell ring: kCellFields x kRing
   T *const fr = sm + kCellFields * kRing;                   // face ring: kFaceFields x kRing
@@ -463,7 +500,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           lm = lamg[0]; l0 = lamg[1]; lp = lamg[2];
         } else {
 #pragma unroll
-          for (int q = 1; q <= 6; ++q) {
+          for (int q = Q0; q < Q0 + NS; ++q) {
             const T U = CELL(CF_UC, q), ac = CELL(CF_AC, q);
             lm = fmax(lm, fabs(U - ac));
             l0 = fmax(l0, fabs(U));
@@ -529,8 +566,8 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           c[4] = X4 - Y4;
         };
 
-        // split stencil values f+/- for m = i-2..i+3
-        T fpl[6][5], fmi[6][5];
+        // split stencil values f+/- for the NS stencil points
+        T fpl[NS][5], fmi[NS][5];
         // f+- = (1/2) l.(dF +- lambda d (1/J)_m) of one stencil point
         auto split_point = [&](int s, const T dF[5], const T d[5], T ijm) {
           T cF[5], cD[5];
@@ -547,8 +584,8 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         if (fpform) {
           // reference-state differences of the stencil points two at a time (packed)
 #pragma unroll
-          for (int s = 0; s < 6; s += 2) {
-            const int q = s + 1, q2 = s + 2;
+          for (int s = 0; s < NS; s += 2) {
+            const int q = s + Q0, q2 = s + Q0 + 1;
             P dp[5], kp2[3], uBp[3], out[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v)
@@ -569,8 +606,8 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         } else {
           // plain scheme: F~_m and Q~_m themselves
 #pragma unroll
-          for (int s = 0; s < 6; ++s) {
-            const int q = s + 1;
+          for (int s = 0; s < NS; ++s) {
+            const int q = s + Q0;
             T dF[5], d[5];
             const T km[3] = {CELL(CF_K, q), CELL(CF_K + 1, q), CELL(CF_K + 2, q)};
             const T uB[3] = {CELL(CF_U, q), CELL(CF_U + 1, q), CELL(CF_U + 2, q)};
@@ -591,10 +628,18 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         T h[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          const P r = recon5_pair<T, SCHEME>(pmk(fpl[0][v], fmi[5][v]), pmk(fpl[1][v], fmi[4][v]),
-                                             pmk(fpl[2][v], fmi[3][v]), pmk(fpl[3][v], fmi[2][v]),
-                                             pmk(fpl[4][v], fmi[1][v]));
-          h[v] = r.x + r.y;
+          if constexpr (SCHEME == 2) {
+            P w7[7];
+#pragma unroll
+            for (int t = 0; t < 7; ++t) w7[t] = pmk(fpl[t][v], fmi[7 - t][v]);   // i-3..i+3 / i+4..i-2
+            const P r = recon7_pair<T>(w7);
+            h[v] = r.x + r.y;
+          } else {
+            const P r = recon5_pair<T, SCHEME>(pmk(fpl[0][v], fmi[5][v]), pmk(fpl[1][v], fmi[4][v]),
+                                               pmk(fpl[2][v], fmi[3][v]), pmk(fpl[3][v], fmi[2][v]),
+                                               pmk(fpl[4][v], fmi[1][v]));
+            h[v] = r.x + r.y;
+          }
         }
         T F[5];
         if (charwise) {
@@ -719,6 +764,7 @@ cudaError_t launch_sweep_t(const SweepLaunch &L, int M, int scheme, int charwise
   if (M == MM && scheme == SS) return launch_one<T, MM, SS>(L, charwise, fp, s);
   FPK_CASE(2, 0) FPK_CASE(4, 0) FPK_CASE(6, 0) FPK_CASE(8, 0)
   FPK_CASE(2, 1) FPK_CASE(4, 1) FPK_CASE(6, 1) FPK_CASE(8, 1)
+  FPK_CASE(2, 2) FPK_CASE(4, 2) FPK_CASE(6, 2) FPK_CASE(8, 2)
 #undef FPK_CASE
   return cudaErrorInvalidValue;
 }
@@ -738,6 +784,7 @@ int prepare_t(int M, int scheme) {
   }
   FPK_OCC(2, 0) FPK_OCC(4, 0) FPK_OCC(6, 0) FPK_OCC(8, 0)
   FPK_OCC(2, 1) FPK_OCC(4, 1) FPK_OCC(6, 1) FPK_OCC(8, 1)
+  FPK_OCC(2, 2) FPK_OCC(4, 2) FPK_OCC(6, 2) FPK_OCC(8, 2)
 #undef FPK_OCC
   return nb > 0 ? nb : 1;
 }

@@ -32,17 +32,18 @@ BC_FARFIELD = 1
 BC_EXTRAP = 2
 
 
-def ghost_width(metric_order: int) -> int:
-    """State/metric ghost width G = max(3, M/2): the WENO5 stencil reaches
-    three points and the order-M face interpolation M/2 points past a face."""
-    return max(3, metric_order // 2)
+def ghost_width(metric_order: int, scheme: int = 0) -> int:
+    """State/metric ghost width G = max(3, M/2): the five-point upwind stencils
+    reach three points and the order-M face interpolation M/2 points past a
+    face.  The seven-point WENO stencil (scheme 2) reaches four points."""
+    return max(4 if scheme == 2 else 3, metric_order // 2)
 
 
-def node_ghost_width(metric_order: int) -> int:
+def node_ghost_width(metric_order: int, scheme: int = 0) -> int:
     """Node ghost width needed to evaluate metrics and Jacobian by the same
     central operators in every state ghost cell: G + 3M/2 (inner derivative,
     outer derivative of the metric products, derivative in the Jacobian)."""
-    return ghost_width(metric_order) + 3 * (metric_order // 2)
+    return ghost_width(metric_order, scheme) + 3 * (metric_order // 2)
 
 
 @dataclasses.dataclass

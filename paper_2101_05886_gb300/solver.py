@@ -28,7 +28,7 @@ class Block:
                                 precision, grid.bc, gamma, q_inf, global_lf)
         nodes = np.ascontiguousarray(grid.nodes, dtype=np.float64)
         self.ctx = B.fp_init_grid(self.desc, nodes.ctypes.data, int(grid.Gn), _stream())
-        self.G = B.fp_ghost_width(metric_order)
+        self.G = B.fp_ghost_width(metric_order, scheme)
 
     @property
     def shape(self):

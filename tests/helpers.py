@@ -26,6 +26,23 @@ def rel_err(gpu, ora, floor_frac=FLOOR_FRAC, per_component=False):
     return errs if per_component else max(errs)
 
 
+def ulp_sensitivity(cfg, met, q, draws=3, seed=0):
+    """Conditioning of the residual at q: the largest parity metric between the
+    oracle's dq/dt at q and at q with every entry moved by one unit in the last
+    place (random sign), over a few draws.  Two correct FP64 evaluations that round
+    differently can disagree by about this much; WENO7-JS, whose nonlinear weights
+    react to smoothness indicators with coefficients up to 5188/240, is about a
+    hundred times more sensitive than WENO5-JS on the same input."""
+    _, d0 = O.rhs(cfg, met, q)
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(draws):
+        qp = q * (1.0 + np.finfo(np.float64).eps * rng.choice([-1.0, 1.0], size=q.shape))
+        _, d1 = O.rhs(cfg, met, qp)
+        worst = max(worst, rel_err(d1, d0))
+    return worst
+
+
 def oracle_subbox_dqdt(grid, q, M, lo, size, scheme=0, fp=1, charwise=1, gamma=1.4, qinf=None):
     """dQ/dt of the oracle on an interior sub-box [lo, lo+size) of a 3-D grid.
 

@@ -33,6 +33,8 @@ def test_library_exports_every_declared_symbol(lib):
 def test_ghost_widths(lib):
     assert [B.fp_ghost_width(m) for m in (2, 4, 6, 8)] == [3, 3, 3, 4]
     assert [B.fp_node_ghost_width(m) for m in (2, 4, 6, 8)] == [6, 9, 12, 16]
+    assert [B.fp_ghost_width(m, B.FP_WENO7_JS) for m in (2, 4, 6, 8)] == [4, 4, 4, 4]
+    assert [B.fp_node_ghost_width(m, B.FP_WENO7_JS) for m in (2, 4, 6, 8)] == [7, 10, 13, 16]
 
 
 def test_status_strings(lib):
@@ -40,7 +42,7 @@ def test_status_strings(lib):
         assert lib.fp_status_string(st)
 
 
-@pytest.mark.parametrize("field,value", [("dims", 4), ("metric_order", 5), ("scheme", 7), ("precision", 3),
+@pytest.mark.parametrize("field,value", [("dims", 4), ("metric_order", 5), ("scheme", 3), ("precision", 3),
                                          ("gamma", 0.9), ("characteristic", 2), ("free_stream_preserving", -1)])
 def test_invalid_descriptor_is_rejected_before_any_gpu_work(lib, field, value):
     d = B.make_desc(3, (8, 8, 8), metric_order=6)

@@ -8,7 +8,7 @@ torch = pytest.importorskip("torch")
 
 import oracle as O
 from paper_2101_05886_gb300 import inputs as I
-from tests.helpers import oracle_subbox_dqdt, rel_err
+from tests.helpers import oracle_subbox_dqdt, rel_err, ulp_sensitivity
 
 pytestmark = pytest.mark.gpu
 
@@ -21,8 +21,8 @@ from paper_2101_05886_gb300.solver import Batch, Block  # noqa: E402
 F64, F32 = B.FP_F64, B.FP_F32_MIXED
 
 
-def _case(name, M):
-    Gn = O.node_ghost(M)
+def _case(name, M, scheme=0):
+    Gn = O.node_ghost(M, scheme)
     if name == "2d_config1":
         g = I.wavy_sinsin_2d(n=33, amp=0.1, jitter=0.01, seed=1, Gn=Gn)
         qinf = I.uniform_qinf(0.5, 30.0)
@@ -45,7 +45,7 @@ def _case(name, M):
         qinf = I.uniform_qinf(3.0, 0.0)
         q = I.random_smooth_state(g, qinf, amp=0.03, seed=4)
     elif name == "3d_min":
-        G = O.ghost(M)
+        G = O.ghost(M, scheme)
         g = I.periodic_wavy_3d((G, G + 1, G + 2), L=1.0, amp=0.05, Gn=Gn)
         qinf = I.uniform_qinf(0.6, 10.0, 5.0)
         q = I.random_smooth_state(g, qinf, amp=0.05, seed=9)
@@ -351,3 +351,117 @@ def test_shock_on_randomised_grid_parity_and_no_overshoot(frac):
     assert rho.min() > r1 - 0.05 * (r2 - r1) and rho.max() < r2 + 0.05 * (r2 - r1)
     assert blk.status() == B.FP_OK
     blk.close()
+
+
+# ---- WENO7-JS under the same free-stream-preserving wrapper (Remark 2) ----
+WENO7_CASES = [
+    ("2d_vortex", 8, 1, 1), ("2d_ragged", 4, 1, 1), ("3d_vortex", 6, 1, 1), ("3d_vortex", 8, 1, 1),
+    ("3d_vortex", 6, 0, 1), ("3d_vortex", 8, 1, 0), ("3d_ogrid", 4, 1, 1), ("3d_min", 8, 1, 1), ("3d_min", 2, 1, 1),
+]
+
+
+def _weno7_tol(cfg, met, q):
+    """FP64 bound for WENO7: 1e-12, or twice the residual's response to one-ulp input
+    perturbations when that is larger (the WENO7 weights amplify rounding about a
+    hundred times more than the WENO5 ones; measured 2e-12 to 4e-11 on these cases)."""
+    return max(1e-12, 2.0 * ulp_sensitivity(cfg, met, q))
+
+
+@pytest.mark.parametrize("name,M,charwise,fp", WENO7_CASES)
+def test_weno7_rhs_parity_fp64(name, M, charwise, fp):
+    W7 = B.FP_WENO7_JS
+    g, qinf, q = _case(name, M, W7)
+    blk = Block(g, metric_order=M, scheme=W7, fp=fp, characteristic=charwise, precision=F64, q_inf=qinf)
+    assert blk.G == O.ghost(M, W7)
+    dq = blk.rhs(blk.to_device(q)).cpu().numpy()
+    cfg = O.cfg_for(g, M=M, scheme=W7, fp=fp, charwise=charwise, qinf=qinf)
+    met = O.metrics(cfg, g.nodes, g.Gn)
+    _, dqo = O.rhs(cfg, met, q)
+    errs = rel_err(dq, dqo, per_component=True)
+    tol = _weno7_tol(cfg, met, q)
+    assert tol <= 1e-10
+    assert max(errs) <= tol, (errs, tol)
+    blk.close()
+
+
+@pytest.mark.parametrize("name,M", [("2d_vortex", 8), ("3d_vortex", 6), ("3d_ogrid", 8)])
+def test_weno7_rhs_parity_fp32_mixed(name, M):
+    W7 = B.FP_WENO7_JS
+    g, qinf, q = _case(name, M, W7)
+    q32 = q.astype(np.float32).astype(np.float64)
+    blk = Block(g, metric_order=M, scheme=W7, precision=F32, q_inf=qinf)
+    dq = blk.rhs(blk.to_device(q32)).cpu().numpy()
+    cfg = O.cfg_for(g, M=M, scheme=W7, qinf=qinf)
+    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q32)
+    errs = rel_err(dq, dqo, per_component=True)
+    assert max(errs) <= 1e-5, errs
+    blk.close()
+
+
+def test_weno7_rk3_and_global_lf_parity_fp64():
+    W7 = B.FP_WENO7_JS
+    g, qinf, q = _case("3d_vortex", 8, W7)
+    cfg = O.cfg_for(g, M=8, scheme=W7, qinf=qinf, global_lf=1)
+    met = O.metrics(cfg, g.nodes, g.Gn)
+    blk = Block(g, metric_order=8, scheme=W7, precision=F64, q_inf=qinf, global_lf=1)
+    dq = blk.rhs(blk.to_device(q)).cpu().numpy()
+    _, dqo = O.rhs(cfg, met, q)
+    tol = _weno7_tol(cfg, met, q)
+    assert max(rel_err(dq, dqo, per_component=True)) <= tol
+    dt = 0.5 * O.cfl_dt(cfg, met, q, 0.5)
+    qd = blk.to_device(q)
+    qo = q.copy()
+    for _ in range(2):
+        blk.rk3_step(qd, dt)
+        qo = O.rk3_step(cfg, met, qo, dt)
+    assert rel_err(qd.cpu().numpy() - q, qo - q) <= max(1e-11, tol)
+    assert blk.status() == B.FP_OK
+    blk.close()
+
+
+@pytest.mark.parametrize("precision,M", [(F64, 6), (F64, 8), (F32, 6), (F32, 8)])
+def test_weno7_config1_free_stream_ten_steps(precision, M):
+    """Free stream on the wavy, jittered Config-1 grid with WENO7-M6/M8 (the
+    paper's Table 1 rows): FP64 drift at rounding level, FP32 drift exactly zero."""
+    W7 = B.FP_WENO7_JS
+    g = I.wavy_sinsin_2d(n=33, amp=0.1, jitter=0.01, seed=1, Gn=O.node_ghost(M, W7))
+    qinf = I.uniform_qinf(0.5, 30.0)
+    blk = Block(g, metric_order=M, scheme=W7, precision=precision, q_inf=qinf)
+    qd = blk.to_device(I.uniform_state(g, qinf))
+    ref = qd.clone()
+    dt = blk.cfl_dt(qd, 0.5)
+    for _ in range(10):
+        blk.rk3_step(qd, dt)
+    torch.cuda.synchronize()
+    drift = (qd - ref).abs().max().item() / np.abs(qinf).max()
+    if precision == F32:
+        assert drift == 0.0
+    else:
+        assert drift < 1e-13
+    blk.close()
+
+
+def test_weno7_batch_matches_single_blocks_bitwise():
+    W7 = B.FP_WENO7_JS
+    M = 8
+    Gn = O.node_ghost(M, W7)
+    grids = [I.periodic_wavy_3d((20 + 3 * b, 17, 13 + b), L=10.0, amp=0.08, Gn=Gn) for b in range(3)]
+    qinf = I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0)
+    blocks, qs, refs = [], [], []
+    for g in grids:
+        q = I.vortex_3d(g, mach=0.8, eps=5.0, L=10.0).astype(np.float32).astype(np.float64)
+        b1 = Block(g, metric_order=M, scheme=W7, precision=F32, q_inf=qinf)
+        b2 = Block(g, metric_order=M, scheme=W7, precision=F32, q_inf=qinf)
+        q1, q2 = b1.to_device(q), b2.to_device(q)
+        b1.rk3_step(q1, 1e-3)
+        blocks.append(b2)
+        qs.append(q2)
+        refs.append(q1)
+    bat = Batch(blocks, qs, autotune=0)
+    bat.rk3_step(1e-3)
+    torch.cuda.synchronize()
+    for a, r in zip(qs, refs):
+        assert torch.equal(a, r)
+    bat.close()
+    for b in blocks:
+        b.close()
