@@ -39,7 +39,7 @@ class Cfg(ctypes.Structure):
                 ("scheme", ctypes.c_int), ("fp", ctypes.c_int), ("charwise", ctypes.c_int),
                 ("form", ctypes.c_int), ("global_lf", ctypes.c_int), ("bc", (ctypes.c_int * 2) * 3),
                 ("gamma", ctypes.c_double),
-                ("qinf", ctypes.c_double * 5)]
+                ("qinf", ctypes.c_double * 5), ("cut", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -83,7 +83,7 @@ def _p(a: np.ndarray):
 
 
 def make_cfg(dims, n, M=6, scheme=0, fp=1, charwise=1, form=2, bc=((0, 0), (0, 0), (0, 0)),
-             gamma=1.4, qinf=(1.4, 0.0, 0.0, 0.0, 2.5), global_lf=0) -> Cfg:
+             gamma=1.4, qinf=(1.4, 0.0, 0.0, 0.0, 2.5), global_lf=0, cut=0) -> Cfg:
     c = Cfg()
     c.dims = dims
     for d in range(3):
@@ -92,6 +92,7 @@ def make_cfg(dims, n, M=6, scheme=0, fp=1, charwise=1, form=2, bc=((0, 0), (0, 0
         c.bc[d][1] = int(bc[d][1])
     c.M, c.scheme, c.fp, c.charwise, c.form = M, scheme, fp, charwise, form
     c.global_lf = global_lf
+    c.cut = int(cut)
     c.gamma = gamma
     for v in range(5):
         c.qinf[v] = float(qinf[v])
@@ -101,7 +102,8 @@ def make_cfg(dims, n, M=6, scheme=0, fp=1, charwise=1, form=2, bc=((0, 0), (0, 0
 def cfg_for(grid, M=6, scheme=0, fp=1, charwise=1, form=2, gamma=1.4, qinf=None, global_lf=0) -> Cfg:
     if qinf is None:
         qinf = (1.4, 0.0, 0.0, 0.0, 2.5)
-    return make_cfg(grid.dims, grid.n, M, scheme, fp, charwise, form, grid.bc, gamma, qinf, global_lf)
+    return make_cfg(grid.dims, grid.n, M, scheme, fp, charwise, form, grid.bc, gamma, qinf, global_lf,
+                    getattr(grid, "cut", 0))
 
 
 def ghost(M: int, scheme: int = 0) -> int:

@@ -150,6 +150,9 @@ static int valid_cfg(const or_cfg *c) {
   if (c->scheme < 0 || c->scheme > 2) return 0;
   for (int d = 0; d < 3; ++d) if (c->n[d] < 1) return 0;
   if (c->dims == 2 && c->n[2] != 1) return 0;
+  for (int d = 0; d < c->dims; ++d)
+    for (int s = 0; s < 2; ++s) if (c->bc[d][s] < 0 || c->bc[d][s] > 4) return 0;
+  if (c->cut < 0) return 0;
   return 1;
 }
 
@@ -565,7 +568,24 @@ static void face_flux_impl(const or_cfg *c, const double q8[40], const double me
 /* ------------------------------------------------------------------------ */
 static int wrap(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
 
-static double *ghost_state(const or_cfg *c, const double *q, int G, int lo[3], int hi[3]) {
+/* unit normal n = k/|k| of the boundary face of direction d on side s of the grid line
+   through p, with k the order-M face metric (Sec. 3, Eq. xidJ) */
+static void boundary_normal(const or_cfg *c, const double *met, const arr3 *A, size_t nb, int d, int s,
+                            const int p[3], double nrm[3]) {
+  double w[8], k[3] = {0.0, 0.0, 0.0};
+  or_interp_coef(c->M, w);
+  const int f = s ? c->n[d] - 1 : -1;          /* face f+1/2 */
+  for (int m = 0; m < c->M; ++m) {
+    int r[3] = {p[0], p[1], p[2]};
+    r[d] = f - c->M / 2 + 1 + m;
+    const size_t o = at3(A, r[0], r[1], r[2]);
+    for (int a = 0; a < 3; ++a) k[a] += w[m] * met[(size_t)(3 * d + a) * nb + o];
+  }
+  const double len = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+  for (int a = 0; a < 3; ++a) nrm[a] = k[a] / len;
+}
+
+static double *ghost_state(const or_cfg *c, const double *met, const double *q, int G, int lo[3], int hi[3]) {
   for (int d = 0; d < 3; ++d) {
     int on = d < c->dims;
     lo[d] = on ? -G : 0;
@@ -579,22 +599,42 @@ static double *ghost_state(const or_cfg *c, const double *q, int G, int lo[3], i
     for (int j = lo[1]; j < hi[1]; ++j)
       for (int i = lo[0]; i < hi[0]; ++i) {
         int p[3] = {i, j, k}, src[3];
-        int far = 0;
+        int far = 0, nwall = 0, wd[3], ws[3];
+        for (int d = 0; d < 3; ++d) src[d] = p[d];
         for (int d = 0; d < 3; ++d) {
-          src[d] = p[d];
           if (p[d] < 0 || p[d] >= c->n[d]) {
             int side = p[d] < 0 ? 0 : 1;
             int b = c->bc[d][side];
+            const int mirror = side ? 2 * c->n[d] - 1 - p[d] : -1 - p[d];
             if (b == 0) src[d] = wrap(p[d], c->n[d]);
             else if (b == 1) far = 1;
-            else src[d] = p[d] < 0 ? 0 : c->n[d] - 1;
+            else if (b == 2) src[d] = p[d] < 0 ? 0 : c->n[d] - 1;
+            else {
+              const int t = d == 0 ? 1 : 0;           /* direction reversed through a cut */
+              const int tt = p[t] < 0 ? 0 : (p[t] >= c->n[t] ? c->n[t] - 1 : p[t]);
+              src[d] = mirror;
+              if (b == 4 && (tt < c->cut || tt >= c->n[t] - c->cut)) {
+                src[t] = c->n[t] - 1 - p[t];
+              } else {
+                wd[nwall] = d; ws[nwall] = side; ++nwall;
+              }
+            }
           }
         }
+        for (int d = 0; d < 3; ++d)                   /* corner points: clamp what is left */
+          if (src[d] < 0 || src[d] >= c->n[d]) src[d] = src[d] < 0 ? 0 : c->n[d] - 1;
         size_t o = at3(&A, i, j, k);
+        double Q[5];
         for (int v = 0; v < 5; ++v)
-          g[(size_t)v * nb + o] =
-              far ? c->qinf[v]
-                  : q[(size_t)v * ni * nj * nk + ((size_t)src[2] * nj + src[1]) * ni + src[0]];
+          Q[v] = far ? c->qinf[v]
+                     : q[(size_t)v * ni * nj * nk + ((size_t)src[2] * nj + src[1]) * ni + src[0]];
+        for (int w = 0; w < nwall && !far; ++w) {
+          double nrm[3];
+          boundary_normal(c, met, &A, nb, wd[w], ws[w], p, nrm);
+          const double mn = Q[1] * nrm[0] + Q[2] * nrm[1] + Q[3] * nrm[2];
+          for (int a = 0; a < 3; ++a) Q[1 + a] -= 2.0 * mn * nrm[a];
+        }
+        for (int v = 0; v < 5; ++v) g[(size_t)v * nb + o] = Q[v];
       }
   return g;
 }
@@ -604,7 +644,7 @@ int or_rhs(const or_cfg *c, const double *met, const double *q, double *R, doubl
   const int G = or_ghost_s(c->M, c->scheme);
   for (int d = 0; d < c->dims; ++d) if (c->n[d] < G) return 1;
   int lo[3], hi[3];
-  double *g = ghost_state(c, q, G, lo, hi);
+  double *g = ghost_state(c, met, q, G, lo, hi);
   arr3 A = {{lo[0], lo[1], lo[2]}, {hi[0], hi[1], hi[2]}, NULL};
   size_t nb = box_size(lo, hi);
   const int ni = c->n[0], nj = c->n[1], nk = c->n[2];

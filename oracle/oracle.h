@@ -32,10 +32,23 @@ typedef struct {
   int charwise;    /* 1 = characteristic-wise (Roe eigenvectors), 0 = component-wise */
   int form;        /* 2 = WENO(F_m - F*_m + F*_face) (Eq. my_point2), 1 = WENO(F_m - F*_m) + F*_face (Eq. my_point1) */
   int global_lf;   /* 0 = local Lax-Friedrichs speeds (stencil max), 1 = global (max over the block) */
-  int bc[3][2];    /* 0 periodic, 1 far field (q_inf), 2 zero gradient */
+  int bc[3][2];    /* 0 periodic, 1 far field (q_inf), 2 zero gradient, 3 slip wall,
+                      4 C-grid cut (see below) */
   double gamma;
   double qinf[5];
+  int cut;         /* code 4 only: cells t < cut and t >= n_t - cut of the reversed direction t
+                      connect across the cut; the cells in between are slip wall */
 } or_cfg;
+
+/* Boundary rules for a ghost point at index x of direction d (x < 0 on side 0, x >= n_d on
+   side 1), with the mirror index x' = -1 - x (side 0) or 2 n_d - 1 - x (side 1):
+   - 3 slip wall: the wall is the boundary face; the ghost state is the state at x' with its
+     momentum reflected about that face's unit normal n = k/|k| (k = the order-M face metric
+     of direction d at the boundary face of the same grid line): m - 2 (m.n) n.
+   - 4 C-grid cut: the boundary face of direction d is a cut through which the block meets
+     itself with the transverse index t reversed (t = j for d = 0, t = i for d = 1, 2): the
+     ghost state is the state at (x', t' = n_t - 1 - t) as it is.  Points with
+     cut <= t < n_t - cut use the slip-wall rule instead (the body of a C-grid). */
 
 int or_ghost(int M);                 /* G = max(3, M/2) for the 5th-order schemes */
 int or_node_ghost(int M);            /* G + 3M/2 */

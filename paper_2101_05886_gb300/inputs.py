@@ -30,6 +30,8 @@ GAMMA = 1.4
 BC_PERIODIC = 0
 BC_FARFIELD = 1
 BC_EXTRAP = 2
+BC_SLIP_WALL = 3
+BC_CUT = 4
 
 
 def ghost_width(metric_order: int, scheme: int = 0) -> int:
@@ -55,6 +57,7 @@ class Grid:
     nodes: np.ndarray   # [dims][..][..] float64 with Gn ghosts
     bc: tuple           # ((lo,hi) for i, (lo,hi) for j, (lo,hi) for k)
     name: str = ""
+    cut: int = 0        # BC_CUT sides: cells t < cut and t >= n_t - cut meet across the cut
 
     def interior_xyz(self):
         """Coordinates of the solution points, each shaped like one state component."""
@@ -212,19 +215,62 @@ def periodic_wavy_3d(n, L=10.0, amp=0.08, Gn=6, dtype=np.float64):
     return Grid(3, (ni, nj, nk), Gn, nodes, (b, b, b), "periodic_wavy_3d")
 
 
-def cylinder_ogrid(n, r0=0.5, r1=20.0, beta=3.0, Lz=4.0, Gn=6):
+def cylinder_ogrid(n, r0=0.5, r1=20.0, beta=3.0, Lz=4.0, Gn=6, wall=False):
     """Cylinder O-grid: i runs around the cylinder (periodic), j is radial with a
-    tanh stretch r = r0 + (r1-r0)[1 - tanh(beta(1-eta'))/tanh(beta)], eta' = j/(nj-1),
-    k is spanwise (periodic with offset Lz).  Wall side (j=0) is zero-gradient,
-    outer side (j=nj-1) far field."""
+    tanh stretch r = r0 + (r1-r0)[1 - tanh(beta(1-eta'))/tanh(beta)], k is spanwise
+    (periodic with offset Lz); the outer side (j=nj-1) is far field.
+    wall=False: eta' = j/(nj-1), the first points lie on r = r0, zero-gradient there.
+    wall=True: eta' = (j+1/2)/(nj-1/2), so r = r0 is the face j = -1/2, a slip wall."""
     ni, nj, nk = n
     KK, JJ, II = _mesh3(ni, nj, nk, Gn)
     th = 2 * np.pi * II / ni
-    ep = JJ / (nj - 1)
+    ep = (JJ + 0.5) / (nj - 0.5) if wall else JJ / (nj - 1)
     r = r0 + (r1 - r0) * (1.0 - np.tanh(beta * (1.0 - ep)) / np.tanh(beta))
     nodes = np.ascontiguousarray(np.stack([r * np.cos(th), r * np.sin(th), Lz * KK / nk]))
-    bc = ((BC_PERIODIC, BC_PERIODIC), (BC_EXTRAP, BC_FARFIELD), (BC_PERIODIC, BC_PERIODIC))
-    return Grid(3, (ni, nj, nk), Gn, nodes, bc, "cylinder_ogrid")
+    bc = ((BC_PERIODIC, BC_PERIODIC), (BC_SLIP_WALL if wall else BC_EXTRAP, BC_FARFIELD),
+          (BC_PERIODIC, BC_PERIODIC))
+    return Grid(3, (ni, nj, nk), Gn, nodes, bc, "cylinder_ogrid_wall" if wall else "cylinder_ogrid")
+
+
+def mirror_channel_2d(n, amp=0.06, Gn=6, doubled=False):
+    """Wavy channel for the slip-wall checks: xi' = i/ni periodic in i (x offset 1),
+    eta'_j = (j + 1/2)/nj, x = xi' + amp sin(2 pi xi') cos(2 pi eta'),
+    y = eta' + amp sin(2 pi xi') sin(2 pi eta').  The map is mirror symmetric about
+    eta' = 0 and eta' = 1 (x even, y odd), the faces j = -1/2 and j = nj - 1/2, so the
+    ghost nodes are the mirror images of the interior nodes.
+    doubled=False: walls on both j sides.  doubled=True: the mirror-doubled channel
+    eta' in [-1, 1) (2 nj points, j - nj in place of j), periodic in j with y offset 2."""
+    ni, nj = n
+    nj2 = 2 * nj if doubled else nj
+    I = _index_range(ni, Gn)
+    J = _index_range(nj2, Gn)
+    JJ, II = np.meshgrid(J, I, indexing="ij")
+    xi = II / ni
+    eta = ((JJ - nj) if doubled else JJ) / nj + 0.5 / nj
+    sx = amp * np.sin(2 * np.pi * xi)
+    nodes = np.ascontiguousarray(np.stack([xi + sx * np.cos(2 * np.pi * eta), eta + sx * np.sin(2 * np.pi * eta)]))
+    bj = (BC_PERIODIC, BC_PERIODIC) if doubled else (BC_SLIP_WALL, BC_SLIP_WALL)
+    return Grid(2, (ni, nj2, 1), Gn, nodes, ((BC_PERIODIC, BC_PERIODIC), bj, (BC_PERIODIC, BC_PERIODIC)),
+                "mirror_channel_2d")
+
+
+def parabolic_cgrid_2d(n, a=1.0, b=1.0, Gn=6):
+    """C-grid of the parabolic map x + i y = (xi' + i eta')^2 with xi'_i = a(2(i+1/2)/ni - 1)
+    (i runs from the lower side of the slit y = 0, x > 0 around the origin to its upper
+    side) and eta'_j = b (j + 1/2)/nj.  The face j = -1/2 is the slit, which the grid meets
+    from both sides: (xi', -eta') and (-xi', eta') are the same point, so the analytic ghost
+    nodes j < 0 are the nodes across the cut (index ni-1-i, -1-j), as the C-grid cut rule
+    expects.  The whole j-lo side is a cut (cut = ni/2, ni even); other sides far field."""
+    ni, nj = n
+    assert ni % 2 == 0
+    I = _index_range(ni, Gn)
+    J = _index_range(nj, Gn)
+    JJ, II = np.meshgrid(J, I, indexing="ij")
+    xs = a * (2.0 * (II + 0.5) / ni - 1.0)
+    es = b * (JJ + 0.5) / nj
+    nodes = np.ascontiguousarray(np.stack([xs * xs - es * es, 2.0 * xs * es]))
+    bc = ((BC_FARFIELD, BC_FARFIELD), (BC_CUT, BC_FARFIELD), (BC_PERIODIC, BC_PERIODIC))
+    return Grid(2, (ni, nj, 1), Gn, nodes, bc, "parabolic_cgrid_2d", cut=ni // 2)
 
 
 def _stretch_beta(first, npts):
@@ -255,7 +301,7 @@ def _growth_ratio(first, total, steps):
 
 
 def cgrid_wing(n=(512, 384, 512), tc=0.15, taper=0.5, sweep_deg=30.0, span=3.0,
-               far=20.0, first_cell=1e-4, wake_frac=0.25, Gn=6, dtype=np.float64):
+               far=20.0, first_cell=1e-4, wake_frac=0.25, Gn=6, dtype=np.float64, physical=True):
     """Single-block C-grid around a swept, tapered, extruded thick wing-like body.
 
     i wraps from the lower wake outflow, around the body (trailing edge -> leading
@@ -271,6 +317,12 @@ def cgrid_wing(n=(512, 384, 512), tc=0.15, taper=0.5, sweep_deg=30.0, span=3.0,
     inner curve along a direction that turns continuously from -y (lower wake)
     through -x (leading edge) to +y (upper wake).  Ghost nodes are the same formulas
     evaluated outside the index ranges.
+    physical=True: the body surface and the wake line are the face j = -1/2 (the wall
+    normal parameter is taken at j + 1/2); the j-lo side is a C-grid cut over the wake
+    cells (i < cut, i >= ni - cut, whose ghost nodes are set to their partners across
+    the cut) and a slip wall over the body, and the root plane k-lo is zero-gradient.
+    physical=False: the first nodes lie on the body and wake line, every j-lo ghost is
+    zero-gradient.
     """
     ni, nj, nk = n
     beta = _stretch_beta(first_cell / far, nj)
@@ -279,7 +331,8 @@ def cgrid_wing(n=(512, 384, 512), tc=0.15, taper=0.5, sweep_deg=30.0, span=3.0,
     k = _index_range(nk, Gn)
     s = i / (ni - 1)                                   # wrap parameter
     z = span * k / (nk - 1)                            # span coordinate
-    sj = 1.0 - np.tanh(beta * (1.0 - j / (nj - 1))) / np.tanh(beta)  # 0 wall, 1 far
+    ej = (j + 0.5) / (nj - 0.5) if physical else j / (nj - 1)
+    sj = 1.0 - np.tanh(beta * (1.0 - ej)) / np.tanh(beta)  # 0 wall, 1 far
     chord = 1.0 - (1.0 - taper) * z / span
     xle = z * math.tan(math.radians(sweep_deg))
     wf = wake_frac
@@ -301,8 +354,17 @@ def cgrid_wing(n=(512, 384, 512), tc=0.15, taper=0.5, sweep_deg=30.0, span=3.0,
         nodes[0, kk] = xin[None, :] + far * sj[:, None] * dx[None, :]
         nodes[1, kk] = yin[None, :] + far * sj[:, None] * dy[None, :]
         nodes[2, kk] = z[kk]
-    bc = ((BC_EXTRAP, BC_EXTRAP), (BC_EXTRAP, BC_FARFIELD), (BC_EXTRAP, BC_EXTRAP))
-    return Grid(3, (ni, nj, nk), Gn, nodes, bc, "cgrid_wing")
+    if not physical:
+        bc = ((BC_EXTRAP, BC_EXTRAP), (BC_EXTRAP, BC_FARFIELD), (BC_EXTRAP, BC_EXTRAP))
+        return Grid(3, (ni, nj, nk), Gn, nodes, bc, "cgrid_wing")
+    cut = int(np.count_nonzero(np.arange(ni) / (ni - 1) < wf))
+    # wake ghost nodes (j < 0, i < cut or i >= ni - cut, ghost i included) are the nodes
+    # across the cut: (i, -1-m) -> (ni-1-i, m)
+    iw = np.concatenate([np.arange(-Gn, cut), np.arange(ni - cut, ni + Gn)])
+    for m in range(Gn):
+        nodes[:, :, Gn - 1 - m, iw + Gn] = nodes[:, :, Gn + m, ni - 1 - iw + Gn]
+    bc = ((BC_EXTRAP, BC_EXTRAP), (BC_CUT, BC_FARFIELD), (BC_EXTRAP, BC_EXTRAP))
+    return Grid(3, (ni, nj, nk), Gn, nodes, bc, "cgrid_wing", cut=cut)
 
 
 def batched_block_sizes(nblocks=64, lo=32, hi=128, seed=4):

@@ -449,9 +449,9 @@ def test_farfield_boundary_sees_q_inf():
 
 
 # ---------------------------------------------------------------- order of accuracy
-def _vortex_complex(x, y, eps=5.0, mach=0.5, gamma=GAMMA):
+def _vortex_complex(x, y, eps=5.0, mach=0.5, gamma=GAMMA, xc=5.0, yc=5.0):
     uinf = mach * np.sqrt(gamma)
-    dx, dy = x - 5.0, y - 5.0
+    dx, dy = x - xc, y - yc
     r2 = dx * dx + dy * dy
     f = eps / (2 * np.pi) * np.exp(0.5 * (1 - r2))
     u, v = uinf - f * dy, f * dx
@@ -677,3 +677,144 @@ def test_remark1_weno7_bitwise_on_cartesian_grid(M):
         cfg = O.cfg_for(g, M=M, scheme=2, fp=fp)
         R[fp] = O.rhs(cfg, O.metrics(cfg, g.nodes, Gn), q)[0]
     assert np.array_equal(R[1], R[0])
+
+
+# ------------------------------------------- boundary rules: slip wall and C-grid cut
+# Sec. 4.2 imposes slip walls (cylinder, airfoils) and uses C-type grids around airfoils
+# without stating the discrete rule.  Reading: the wall (and the cut) is the boundary
+# face; wall ghosts mirror the interior with the momentum reflected about that face's
+# unit normal; cut ghosts are the cells across the cut, taken as they are.
+def _mirror_doubled_state(q):
+    """State on the mirror-doubled channel: rows nj..2nj-1 are q, rows nj-1..0 are q
+    mirrored with the y momentum negated."""
+    low = q[:, :, ::-1, :].copy()
+    low[2] *= -1.0
+    return np.ascontiguousarray(np.concatenate([low, q], axis=2))
+
+
+@pytest.mark.parametrize("M,scheme,charwise", [(2, 0, 1), (6, 0, 1), (6, 1, 0), (8, 2, 1)])
+def test_slip_walls_equal_the_mirror_doubled_periodic_channel(M, scheme, charwise):
+    """Walls on both sides of a wavy channel whose map is mirror symmetric about both
+    walls give the same residual as the doubled channel (periodic, state mirrored with
+    v -> -v) on its upper half, and the mirrored residual on its lower half: brute
+    force against the wall rule, including the normal taken from the face metric."""
+    Gn = O.node_ghost(M, scheme)
+    g1 = I.mirror_channel_2d((24, 16), Gn=Gn)
+    g2 = I.mirror_channel_2d((24, 16), Gn=Gn, doubled=True)
+    qinf = I.uniform_qinf(0.6, 20.0)
+    q1 = I.random_smooth_state(g1, qinf, amp=0.05, seed=3)
+    q2 = _mirror_doubled_state(q1)
+    c1 = O.cfg_for(g1, M=M, scheme=scheme, charwise=charwise, qinf=qinf)
+    c2 = O.cfg_for(g2, M=M, scheme=scheme, charwise=charwise, qinf=qinf)
+    _, d1 = O.rhs(c1, O.metrics(c1, g1.nodes, Gn), q1)
+    _, d2 = O.rhs(c2, O.metrics(c2, g2.nodes, Gn), q2)
+    scale = np.abs(d1).max()
+    assert np.abs(d2[:, :, 16:, :] - d1).max() <= 1e-12 * scale
+    assert np.abs(_mirror_doubled_state(d1) - d2).max() <= 1e-12 * scale
+    # the rule matters: a zero-gradient side gives a different residual
+    c0 = O.cfg_for(g1, M=M, scheme=scheme, charwise=charwise, qinf=qinf)
+    c0.bc[1][0] = I.BC_EXTRAP
+    _, d0 = O.rhs(c0, O.metrics(c0, g1.nodes, Gn), q1)
+    assert np.abs(d0 - d1).max() > 1e-3 * scale
+
+
+def _transpose_2d(g, q):
+    """The same 2-D problem with i <-> j and x <-> y swapped (orientation kept)."""
+    nodes = np.ascontiguousarray(np.stack([g.nodes[1].T, g.nodes[0].T]))
+    qt = np.ascontiguousarray(q.transpose(0, 1, 3, 2)[[0, 2, 1, 3, 4]])
+    bc = (g.bc[1], g.bc[0], g.bc[2])
+    return I.Grid(2, (g.n[1], g.n[0], 1), g.Gn, nodes, bc, g.name + "_T", g.cut), qt
+
+
+def test_slip_walls_in_the_xi_direction_and_in_3d():
+    """The wall rule in the i direction (transposed channel) and in 3-D (the channel
+    extruded in z, with spanwise momentum): both equal the wall-in-j 2-D result."""
+    M = 6
+    Gn = O.node_ghost(M)
+    g = I.mirror_channel_2d((20, 14), Gn=Gn)
+    qinf = I.uniform_qinf(0.6, 20.0)
+    q = I.random_smooth_state(g, qinf, amp=0.05, seed=5)
+    c = O.cfg_for(g, M=M, qinf=qinf)
+    _, d = O.rhs(c, O.metrics(c, g.nodes, Gn), q)
+    gt, qt = _transpose_2d(g, q)
+    ct = O.cfg_for(gt, M=M, qinf=qinf)
+    _, dt = O.rhs(ct, O.metrics(ct, gt.nodes, Gn), qt)
+    assert np.abs(dt.transpose(0, 1, 3, 2)[[0, 2, 1, 3, 4]] - d).max() <= 1e-12 * np.abs(d).max()
+    # 3-D: extruded channel, state uniform in z with a spanwise momentum added
+    g3 = I.extrude_2d(g, 6, dz=0.05)
+    q3 = np.repeat(q, 6, axis=1)
+    w = 0.1 * q3[0]
+    q3[4] += 0.5 * w * w / q3[0]
+    q3[3] = w
+    g3d = I.mirror_channel_2d((20, 14), Gn=Gn, doubled=True)
+    g3d = I.extrude_2d(g3d, 6, dz=0.05)
+    c3 = O.cfg_for(g3, M=M, qinf=qinf)
+    c3d = O.cfg_for(g3d, M=M, qinf=qinf)
+    _, d3 = O.rhs(c3, O.metrics(c3, g3.nodes, Gn), np.ascontiguousarray(q3))
+    _, d3d = O.rhs(c3d, O.metrics(c3d, g3d.nodes, Gn), _mirror_doubled_state(q3))
+    assert np.abs(d3d[:, :, 14:, :] - d3).max() <= 1e-12 * np.abs(d3).max()
+
+
+def test_slip_wall_keeps_a_tangent_uniform_stream_and_rejects_a_crossing_one():
+    """A uniform stream along a straight wall is an exact solution (zero residual to
+    rounding); one that crosses the wall is not."""
+    M = 6
+    Gn = O.node_ghost(M)
+    g = I.mirror_channel_2d((20, 14), Gn=Gn)
+    q_along = I.uniform_state(g, I.uniform_qinf(0.7, 0.0))
+    q_cross = I.uniform_state(g, I.uniform_qinf(0.7, 30.0))
+    c = O.cfg_for(g, M=M)
+    met = O.metrics(c, g.nodes, Gn)
+    assert np.abs(O.rhs(c, met, q_along)[1]).max() < 1e-12
+    assert np.abs(O.rhs(c, met, q_cross)[1]).max() > 1e-2
+
+
+def _cut_vortex_error(ni, bc_lo=I.BC_CUT):
+    M, scheme = 6, 1
+    Gn = O.node_ghost(M)
+    g = I.parabolic_cgrid_2d((ni, ni // 2), a=3.0, b=3.0, Gn=Gn)
+    bc = list(map(list, g.bc))
+    bc[1][0] = bc_lo
+    g.bc = tuple(map(tuple, bc))
+    x, y = g.interior_xyz()
+    xc, yc = 4.0, 0.3
+    q = I.shu_vortex(x, y, 0.0, xc, yc, eps=5.0, mach=0.5)
+    c = O.cfg_for(g, M=M, scheme=scheme, qinf=I.uniform_qinf(0.5, 0.0, rho=1.0, p=1.0))
+    L = O.rhs(c, O.metrics(c, g.nodes, Gn), q)[1]
+    exact = -0.5 * np.sqrt(GAMMA) * np.imag(_vortex_complex(x + 1e-30j, y, xc=xc, yc=yc)) / 1e-30
+    # cells whose stencils reach through the cut, in the vortex core
+    rows = np.zeros_like(x, dtype=bool)
+    rows[:, :O.ghost(M), :] = True
+    sel = (rows & ((x - xc) ** 2 + (y - yc) ** 2 < 1.5 ** 2))[None]
+    assert sel.sum() > 0
+    return np.abs((L - exact) * sel).max()
+
+
+def test_cgrid_cut_is_design_order_through_the_cut():
+    """A translating vortex sitting on the cut of a parabolic C-grid: the residual of
+    the cells whose stencils cross the cut converges to the closed-form time derivative
+    at the scheme's order (linear upwind, M6), while a wall or zero-gradient rule there
+    leaves an O(1) error."""
+    e = [_cut_vortex_error(n) for n in (128, 256)]
+    assert 4.3 < np.log2(e[0] / e[1]) < 5.7, e
+    assert _cut_vortex_error(256, I.BC_SLIP_WALL) > 100 * e[1]
+    assert _cut_vortex_error(256, I.BC_EXTRAP) > 100 * e[1]
+
+
+def test_cgrid_cut_preserves_a_uniform_stream_at_incidence():
+    """The cut connects the block to itself: a uniform stream at 30 degrees is kept to
+    rounding (a wall there would deflect it)."""
+    M = 6
+    Gn = O.node_ghost(M)
+    g = I.parabolic_cgrid_2d((32, 16), a=2.0, b=2.0, Gn=Gn)
+    qinf = I.uniform_qinf(0.7, 30.0)
+    q = I.uniform_state(g, qinf)
+    c = O.cfg_for(g, M=M, qinf=qinf)
+    met = O.metrics(c, g.nodes, Gn)
+    assert np.abs(O.rhs(c, met, q)[1]).max() < 1e-12
+    c.cut = 6                                       # middle of the slit becomes a flat-plate wall
+    assert np.abs(O.rhs(c, met, q)[1]).max() > 1e-2
+    q0inf = I.uniform_qinf(0.7, 0.0)                  # ... which a stream along it does not see
+    c0 = O.cfg_for(g, M=M, qinf=q0inf)
+    c0.cut = 6
+    assert np.abs(O.rhs(c0, met, I.uniform_state(g, q0inf))[1]).max() < 1e-12
