@@ -50,7 +50,7 @@ typedef enum {
 enum { FP_WENO5_JS = 0, FP_LINEAR_UPWIND5 = 1, FP_WENO7_JS = 2 };  /* reconstruction: Sec. 2.2.2;
                                                                     WENO7 per Remark 2 */
 enum { FP_F64 = 0, FP_F32_MIXED = 1 };                      /* precision of the sweep */
-enum { FP_BC_PERIODIC = 0, FP_BC_FARFIELD = 1, FP_BC_EXTRAP = 2 };
+enum { FP_BC_PERIODIC = 0, FP_BC_FARFIELD = 1, FP_BC_EXTRAP = 2, FP_BC_SLIP_WALL = 3, FP_BC_CUT = 4 };
 enum { FP_XI = 0, FP_ETA = 1, FP_ZETA = 2 };
 
 typedef struct {
@@ -62,13 +62,27 @@ typedef struct {
   int free_stream_preserving; /* 1 = the paper's FP face flux, 0 = plain scheme (control) */
   int characteristic;         /* 1 = Roe characteristic-wise splitting (paper), 0 = component-wise */
   int precision;              /* FP_F64, or FP_F32_MIXED: metrics built in FP64, sweep in FP32 */
-  int bc[3][2];               /* per direction (lo, hi): FP_BC_PERIODIC | FP_BC_FARFIELD | FP_BC_EXTRAP */
+  int bc[3][2];               /* per direction (lo, hi), ghost values produced on read:
+                                 FP_BC_PERIODIC  wrap around the block;
+                                 FP_BC_FARFIELD  q_inf;
+                                 FP_BC_EXTRAP    copy of the boundary cell (zero gradient);
+                                 FP_BC_SLIP_WALL the wall is the boundary face: ghost x' mirrors
+                                   cell x (-1-x, or 2n-1-x) with its momentum reflected about
+                                   the face's normal k/|k|, k the order-M face metric of that
+                                   grid line (Sec. 4.2 slip walls; the discrete rule is ours);
+                                 FP_BC_CUT       C-grid cut: the boundary face meets the block
+                                   itself with the first transverse index t reversed (t = j for
+                                   the i direction, t = i for j and k): ghost x' is the mirror
+                                   cell on line n_t-1-t, unchanged; lines with
+                                   cut_width <= t < n_t - cut_width are slip wall (the body) */
   double gamma;               /* ratio of specific heats (Sec. 2.1 Eq. EOS: 1.4) */
   double q_inf[5];            /* far-field state; also the reference state of the FP32 form */
   int global_lf;              /* 0 = local Lax-Friedrichs speeds (max over the face's stencil),
                                  1 = global speeds (max over the block, per direction and
                                  characteristic field, refreshed every RK stage); Sec. 4 uses
                                  global splitting for its shock cases */
+  int cut_width;              /* FP_BC_CUT sides only: wake cells at each end of t that meet
+                                 across the cut (>= n_t/2: the whole side is a cut) */
 } fp_grid_desc;
 
 typedef struct fp_ctx fp_ctx;

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfpgb300.so")
 FP_OK, FP_ERR_ARG, FP_ERR_CUDA, FP_ERR_OOM, FP_ERR_NONFINITE, FP_ERR_TIMEOUT, FP_ERR_UNSUPPORTED = range(7)
 FP_WENO5_JS, FP_LINEAR_UPWIND5, FP_WENO7_JS = 0, 1, 2
 FP_F64, FP_F32_MIXED = 0, 1
-FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP = 0, 1, 2
+FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP, FP_BC_SLIP_WALL, FP_BC_CUT = 0, 1, 2, 3, 4
 
 # every symbol include/fp.h declares
 EXPORTS = [
@@ -33,7 +33,7 @@ class fp_grid_desc(ctypes.Structure):
                 ("scheme", ctypes.c_int), ("free_stream_preserving", ctypes.c_int),
                 ("characteristic", ctypes.c_int), ("precision", ctypes.c_int),
                 ("bc", (ctypes.c_int * 2) * 3), ("gamma", ctypes.c_double),
-                ("q_inf", ctypes.c_double * 5), ("global_lf", ctypes.c_int)]
+                ("q_inf", ctypes.c_double * 5), ("global_lf", ctypes.c_int), ("cut_width", ctypes.c_int)]
 
 
 _lib = None
@@ -98,7 +98,7 @@ def _check(st, ctx=None, batch=None):
 
 def make_desc(dims, n, metric_order=6, scheme=FP_WENO5_JS, fp=1, characteristic=1,
               precision=FP_F64, bc=((0, 0), (0, 0), (0, 0)), gamma=1.4,
-              q_inf=(1.4, 0.0, 0.0, 0.0, 2.5), global_lf=0) -> fp_grid_desc:
+              q_inf=(1.4, 0.0, 0.0, 0.0, 2.5), global_lf=0, cut_width=0) -> fp_grid_desc:
     d = fp_grid_desc()
     d.dims = dims
     for k in range(3):
@@ -114,6 +114,7 @@ def make_desc(dims, n, metric_order=6, scheme=FP_WENO5_JS, fp=1, characteristic=
     for v in range(5):
         d.q_inf[v] = float(q_inf[v])
     d.global_lf = int(global_lf)
+    d.cut_width = int(cut_width)
     return d
 
 

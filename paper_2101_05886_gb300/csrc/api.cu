@@ -154,6 +154,7 @@ void fill_dirs(fp_ctx *c) {
   B.status = c->status;
   B.global_lf = c->desc.global_lf;
   B.lamg = c->lamg;
+  B.cut = c->desc.cut_width;
 }
 
 void make_items(const BlockDev &B, int bidx, int d, std::vector<int2> &out) {
@@ -211,7 +212,8 @@ int validate(const fp_grid_desc *d, int ghost_nodes, std::string &why) {
   if (d->global_lf != 0 && d->global_lf != 1) { why = "global_lf must be 0 or 1"; return 0; }
   for (int k = 0; k < d->dims; ++k)
     for (int s = 0; s < 2; ++s)
-      if (d->bc[k][s] < 0 || d->bc[k][s] > 2) { why = "unknown boundary code"; return 0; }
+      if (d->bc[k][s] < 0 || d->bc[k][s] > FP_BC_CUT) { why = "unknown boundary code"; return 0; }
+  if (d->cut_width < 0) { why = "cut_width must be non-negative"; return 0; }
   if (!(d->gamma > 1.0) || !std::isfinite(d->gamma)) { why = "gamma must exceed 1"; return 0; }
   const double rho = d->q_inf[0];
   if (!(rho > 0.0)) { why = "q_inf density must be positive"; return 0; }

@@ -146,6 +146,21 @@ __device__ __forceinline__ typename PairOf<T>::type recon7_pair(const typename P
   return pfma(num, pmk(Num<T>::rcp(den.x), Num<T>::rcp(den.y)), v[3]);
 }
 
+// Slip-wall ghost value (a few cells per line end, kept out of line so the sweep's
+// registers are not spent on it): the mirror cell's state q (component stride qc) with
+// its momentum reflected about the boundary face metric fm (component stride fcs),
+// m - 2 (m.k) k/|k|^2.
+template <typename T>
+__device__ __noinline__ void wall_ghost(const T *q, long long qc, const T *fm, long long fcs, T Q[5]) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Q[v] = __ldg(q + v * qc);
+  const T n0 = fm[0], n1 = fm[fcs], n2 = fm[2 * fcs];
+  const T s = T(2) * (Q[1] * n0 + Q[2] * n1 + Q[3] * n2) / (n0 * n0 + n1 * n1 + n2 * n2);
+  Q[1] -= s * n0;
+  Q[2] -= s * n1;
+  Q[3] -= s * n2;
+}
+
 // Asynchronous global -> shared copies of single elements (sm_80+ cp.async).
 template <typename T>
 __device__ __forceinline__ void cp_async_el(T *smem, const T *gmem) {
@@ -314,6 +329,32 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 
     auto off = [&](int x) -> int { return lbase + (x & wm) * SS; };
 
+    // boundary rule of a cell index x of this line: the source cell xx on the line with
+    // state offset qsrc, or the far-field state (far); `wall` asks for the momentum to be
+    // reflected about the boundary face's normal.  Codes: 0 periodic, 1 far field,
+    // 2 zero gradient, 3 slip wall (mirror cell), 4 C-grid cut (mirror cell on the line
+    // with t1 reversed, wall outside the cut width).
+    auto bc_source = [&](int x, int &xx, long long &qsrc, bool &far, bool &wall) {
+      xx = x; qsrc = qbase; far = false; wall = false;
+      if (x >= 0 && x < nd) return;
+      const int bc = x < 0 ? bclo : bchi;
+      if (bc == 0) { xx = x % nd; if (xx < 0) xx += nd; }
+      else if (bc == 1) far = true;
+      else if (bc == 2) xx = x < 0 ? 0 : nd - 1;
+      else {   // rare path: the line's t1 is recovered from its state offset
+        xx = x < 0 ? -1 - x : 2 * nd - 1 - x;
+        const long long T1 = D->qT1;
+        const int n1 = D->nt1, cw = B->cut;
+        const int s1 = (int)((qbase / T1) % n1);
+        if (bc == 4 && (s1 < cw || s1 >= n1 - cw)) qsrc = qbase + (long long)(n1 - 1 - 2 * s1) * T1;
+        else wall = true;
+      }
+    };
+    // slip-wall ghost: the mirror cell's state with m - 2 (m.k) k/|k|^2, k the face metric
+    // of the boundary face of this line (face -1/2 or nd-1/2)
+    auto load_wall = [&](int x, int xx, T Q[5]) {
+      wall_ghost<T>(qin + qbase + (long long)xx * qsd, qc, fmet + (x < 0 ? 0LL : (long long)nd * fsd), fcs, Q);
+    };
     // global loads of one cell (Q, metric vector, 1/J) with the boundary rule applied
     auto fetch = [&](int x, T Q[5], T k[3], T &invJ) {
       if (x >= -G && x < nd + G) {
@@ -321,19 +362,17 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 #pragma unroll
         for (int a = 0; a < 3; ++a) k[a] = met[(3LL * dir + a) * mc + mo];
         invJ = met[9LL * mc + mo];
-        int xx = x;
-        bool far = false;
-        if (x < 0 || x >= nd) {
-          const int bc = x < 0 ? bclo : bchi;
-          if (bc == 0) { xx = x % nd; if (xx < 0) xx += nd; }
-          else if (bc == 1) far = true;
-          else xx = x < 0 ? 0 : nd - 1;
-        }
+        int xx;
+        long long qsrc;
+        bool far, wall;
+        bc_source(x, xx, qsrc, far, wall);
         if (far) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) Q[v] = qb[v];
+        } else if (wall) {
+          load_wall(x, xx, Q);
         } else {
-          const T *qp = qin + qbase + (long long)xx * qsd;
+          const T *qp = qin + qsrc + (long long)xx * qsd;
 #pragma unroll
           for (int v = 0; v < 5; ++v) Q[v] = __ldg(qp + v * qc);
         }
@@ -384,19 +423,20 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 #pragma unroll
         for (int a = 0; a < 3; ++a) cp_async_el(dst + (5 + a) * kThreads, met + (3LL * dir + a) * mc + mo);
         cp_async_el(dst + 8 * kThreads, met + 9LL * mc + mo);
-        int xx = x;
-        bool far = false;
-        if (x < 0 || x >= nd) {
-          const int bc = x < 0 ? bclo : bchi;
-          if (bc == 0) { xx = x % nd; if (xx < 0) xx += nd; }
-          else if (bc == 1) far = true;
-          else xx = x < 0 ? 0 : nd - 1;
-        }
+        int xx;
+        long long qsrc;
+        bool far, wall;
+        bc_source(x, xx, qsrc, far, wall);
         if (far) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) dst[v * kThreads] = qb[v];
+        } else if (wall) {          // a few cells per line end: loaded and reflected in place
+          T Q[5];
+          load_wall(x, xx, Q);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) dst[v * kThreads] = Q[v];
         } else {
-          const T *qp = qin + qbase + (long long)xx * qsd;
+          const T *qp = qin + qsrc + (long long)xx * qsd;
 #pragma unroll
           for (int v = 0; v < 5; ++v) cp_async_el(dst + v * kThreads, qp + v * qc);
         }

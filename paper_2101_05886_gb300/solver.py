@@ -25,7 +25,7 @@ class Block:
         self.precision = precision
         self.dtype = torch.float32 if precision == B.FP_F32_MIXED else torch.float64
         self.desc = B.make_desc(grid.dims, grid.n, metric_order, scheme, fp, characteristic,
-                                precision, grid.bc, gamma, q_inf, global_lf)
+                                precision, grid.bc, gamma, q_inf, global_lf, getattr(grid, "cut", 0))
         nodes = np.ascontiguousarray(grid.nodes, dtype=np.float64)
         self.ctx = B.fp_init_grid(self.desc, nodes.ctypes.data, int(grid.Gn), _stream())
         self.G = B.fp_ghost_width(metric_order, scheme)

@@ -465,3 +465,98 @@ def test_weno7_batch_matches_single_blocks_bitwise():
     bat.close()
     for b in blocks:
         b.close()
+
+
+# ---- slip wall and C-grid cut (Sec. 4.2 boundaries) ----
+def _wall_cut_case(name, M, scheme=0):
+    Gn = O.node_ghost(M, scheme)
+    if name == "channel_walls":
+        g = I.mirror_channel_2d((24, 16), Gn=Gn)
+        qinf = I.uniform_qinf(0.6, 20.0)
+        q = I.random_smooth_state(g, qinf, amp=0.05, seed=3)
+    elif name == "channel_walls_T":
+        g0 = I.mirror_channel_2d((22, 15), Gn=Gn)
+        qinf = I.uniform_qinf(0.6, 20.0)
+        q0 = I.random_smooth_state(g0, qinf, amp=0.05, seed=4)
+        nodes = np.ascontiguousarray(np.stack([g0.nodes[1].T, g0.nodes[0].T]))
+        q = np.ascontiguousarray(q0.transpose(0, 1, 3, 2)[[0, 2, 1, 3, 4]])
+        g = I.Grid(2, (15, 22, 1), Gn, nodes, (g0.bc[1], g0.bc[0], g0.bc[2]), "channel_T")
+    elif name == "ogrid_wall":
+        g = I.cylinder_ogrid((24, 18, 10), Lz=3.0, Gn=Gn, wall=True)
+        qinf = I.uniform_qinf(3.0, 0.0)
+        q = I.random_smooth_state(g, qinf, amp=0.03, seed=4)
+    elif name == "parabolic_cut":
+        g = I.parabolic_cgrid_2d((48, 24), a=3.0, b=3.0, Gn=Gn)
+        qinf = I.uniform_qinf(0.5, 0.0, rho=1.0, p=1.0)
+        q = I.shu_vortex(*g.interior_xyz(), 0.0, 4.0, 0.3, eps=5.0, mach=0.5)
+    elif name == "parabolic_plate":
+        g = I.parabolic_cgrid_2d((48, 24), a=3.0, b=3.0, Gn=Gn)
+        g.cut = 14
+        qinf = I.uniform_qinf(0.5, 10.0)
+        q = I.random_smooth_state(g, qinf, amp=0.05, seed=6)
+    elif name == "cgrid_wing":
+        g = I.cgrid_wing(n=(48, 24, 16), Gn=Gn)
+        qinf = I.uniform_qinf(0.84, 3.0)
+        q = I.random_smooth_state(g, qinf, amp=0.03, seed=2)
+    else:
+        raise KeyError(name)
+    return g, qinf, q
+
+
+WALL_CUT_CASES = [
+    ("channel_walls", 6, 0, F64, 1e-12), ("channel_walls", 8, 2, F64, None), ("channel_walls", 2, 1, F32, 1e-5),
+    ("channel_walls_T", 6, 0, F64, 1e-12), ("ogrid_wall", 6, 0, F64, 1e-12), ("ogrid_wall", 4, 0, F32, 3e-5),
+    ("parabolic_cut", 6, 0, F64, 1e-12), ("parabolic_cut", 6, 1, F32, 1e-5), ("parabolic_plate", 4, 0, F64, 1e-12),
+    ("cgrid_wing", 6, 0, F64, 1e-12), ("cgrid_wing", 6, 0, F32, 1e-5),
+]
+
+
+@pytest.mark.parametrize("name,M,scheme,precision,tol", WALL_CUT_CASES)
+def test_wall_and_cut_parity(name, M, scheme, precision, tol):
+    g, qinf, q = _wall_cut_case(name, M, scheme)
+    if precision == F32:
+        q = q.astype(np.float32).astype(np.float64)
+    blk = Block(g, metric_order=M, scheme=scheme, precision=precision, q_inf=qinf)
+    dq = blk.rhs(blk.to_device(q)).cpu().numpy()
+    cfg = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf)
+    met = O.metrics(cfg, g.nodes, g.Gn)
+    _, dqo = O.rhs(cfg, met, q)
+    if tol is None:                              # WENO7 in FP64: the conditioning bound
+        tol = _weno7_tol(cfg, met, q)
+    errs = rel_err(dq, dqo, per_component=True)
+    assert max(errs) <= tol, (errs, tol)
+    blk.close()
+
+
+def test_wall_and_cut_rk3_parity_and_batch_bitwise():
+    """RK3 steps on a walled O-grid and a cut C-grid wing advanced together in one batch:
+    equal bit for bit to the blocks stepped one by one, and within 1e-11 of the oracle."""
+    M = 6
+    Gn = O.node_ghost(M)
+    cases = [(I.cylinder_ogrid((26, 20, 12), Lz=3.0, Gn=Gn, wall=True), I.uniform_qinf(3.0, 0.0)),
+             (I.cgrid_wing(n=(48, 24, 16), Gn=Gn), I.uniform_qinf(0.84, 3.0))]
+    singles, batched, qs, refs, cfgs = [], [], [], [], []
+    for k, (g, qinf) in enumerate(cases):
+        q = I.random_smooth_state(g, qinf, amp=0.03, seed=10 + k)
+        b1 = Block(g, metric_order=M, precision=F64, q_inf=qinf)
+        b2 = Block(g, metric_order=M, precision=F64, q_inf=qinf)
+        cfg = O.cfg_for(g, M=M, qinf=qinf)
+        singles.append(b1)
+        batched.append(b2)
+        qs.append(b2.to_device(q))
+        refs.append(b1.to_device(q))
+        cfgs.append((cfg, O.metrics(cfg, g.nodes, g.Gn), q))
+    dt = 0.5 * min(O.cfl_dt(c, m, q, 0.5) for c, m, q in cfgs)
+    bat = Batch(batched, qs, autotune=0)
+    for _ in range(2):
+        bat.rk3_step(dt)
+        for b, r in zip(singles, refs):
+            b.rk3_step(r, dt)
+    torch.cuda.synchronize()
+    for a, r, (c, m, q) in zip(qs, refs, cfgs):
+        assert torch.equal(a, r)
+        qo = O.rk3_step(c, m, O.rk3_step(c, m, q, dt), dt)
+        assert rel_err(a.cpu().numpy() - q, qo - q) <= 1e-11
+    bat.close()
+    for b in singles + batched:
+        b.close()
