@@ -57,6 +57,7 @@ struct fp_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int dims = 3, M = 6, scheme = 0, charwise = 1, fp = 1, is_f32 = 1, global_lf = 0;
+  int bnd[3] = {0, 0, 0};   // some block has a slip-wall or cut side in direction d
   int per_sm = 1, nsm = 152;
   int2 *lam_items = nullptr;
   int nlam_items = 0;
@@ -81,6 +82,10 @@ int bfail(fp_batch *b, int st, const std::string &msg) {
 }
 
 // ghost width: the stencil reach past a face (3, or 4 for WENO7) or the face interpolation's M/2
+// direction d of a block has a slip-wall or cut side (those rules are compiled into a
+// separate sweep variant, so blocks without them run a sweep without their code)
+int has_bnd(const fp_grid_desc &d, int dir) { return d.bc[dir][0] >= FP_BC_SLIP_WALL || d.bc[dir][1] >= FP_BC_SLIP_WALL; }
+
 int ghost_of(int M, int scheme) { return std::max(scheme == FP_WENO7_JS ? 4 : 3, M / 2); }
 
 int prepare(int is_f32, int M, int scheme) {
@@ -386,6 +391,7 @@ static int run_passes(fp_ctx *c, int rk, cudaStream_t s) {
       L.stage = stage;
       L.dt = c->dt_dev;
       L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
+      L.bnd = has_bnd(c->desc, d);
       cudaError_t e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic,
                              c->desc.free_stream_preserving, s);
       if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
@@ -571,6 +577,7 @@ static int batch_pass(fp_batch *b, int d, int mode, int stage, cudaStream_t s) {
   L.stage = stage;
   L.dt = b->dt_dev;
   L.grid = grid_for(b->per_sm, b->nsm, L.nitems);
+  L.bnd = b->bnd[d];
   cudaError_t e = launch(b->is_f32, L, b->M, b->scheme, b->charwise, b->fp, s);
   if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
   return FP_OK;
@@ -644,6 +651,7 @@ int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int
   b->nsm = blocks[0]->nsm;
   for (int k = 0; k < nblocks; ++k) {
     b->ctx.push_back(blocks[k]);
+    for (int d = 0; d < 3; ++d) b->bnd[d] |= has_bnd(blocks[k]->desc, d);
     BlockDev B = blocks[k]->hblk;
     B.q[0] = q_devs[k];
     B.dqdt = nullptr;
@@ -805,6 +813,7 @@ extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream
     L.stage = 0;
     L.dt = c->dt_dev;
     L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
+    L.bnd = has_bnd(c->desc, d);
     e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic, c->desc.free_stream_preserving, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: sweep launch");
   }

@@ -73,6 +73,7 @@ struct SweepLaunch {
   int stage;           // RK stage 0,1,2 (input q[stage], output q[(stage+1)%3])
   const double *dt;    // device scalar
   int grid;            // CTAs of the persistent launch
+  int bnd;             // some block of the launch has a slip-wall or cut side in `dir`
 };
 
 // Launchers (sweep_f32.cu / sweep_f64.cu).  Return cudaError_t of the launch.
@@ -84,6 +85,13 @@ cudaError_t launch_sweep_f32(const SweepLaunch &L, int M, int scheme, int charwi
 // return the resident CTAs per SM of the given variant.
 int prepare_sweep_f64(int M, int scheme);
 int prepare_sweep_f32(int M, int scheme);
+// variants with the slip-wall / cut rules compiled in (sweep_f32_bnd.cu, sweep_f64_bnd.cu)
+cudaError_t launch_sweep_f64_bnd(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
+                                 cudaStream_t s);
+cudaError_t launch_sweep_f32_bnd(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
+                                 cudaStream_t s);
+int prepare_sweep_f64_bnd(int M, int scheme);
+int prepare_sweep_f32_bnd(int M, int scheme);
 
 // Metric construction (metrics.cu), FP64.
 struct MetricJob {

@@ -146,14 +146,10 @@ __device__ __forceinline__ typename PairOf<T>::type recon7_pair(const typename P
   return pfma(num, pmk(Num<T>::rcp(den.x), Num<T>::rcp(den.y)), v[3]);
 }
 
-// Slip-wall ghost value (a few cells per line end, kept out of line so the sweep's
-// registers are not spent on it): the mirror cell's state q (component stride qc) with
-// its momentum reflected about the boundary face metric fm (component stride fcs),
-// m - 2 (m.k) k/|k|^2.
+// Slip-wall reflection of a ghost value (the mirror cell's state Q) about the boundary
+// face metric fm (component stride fcs): m - 2 (m.k) k/|k|^2.
 template <typename T>
-__device__ __noinline__ void wall_ghost(const T *q, long long qc, const T *fm, long long fcs, T Q[5]) {
-#pragma unroll
-  for (int v = 0; v < 5; ++v) Q[v] = __ldg(q + v * qc);
+__device__ __forceinline__ void wall_reflect(T Q[5], const T *fm, long long fcs) {
   const T n0 = fm[0], n1 = fm[fcs], n2 = fm[2 * fcs];
   const T s = T(2) * (Q[1] * n0 + Q[2] * n1 + Q[3] * n2) / (n0 * n0 + n1 * n1 + n2 * n2);
   Q[1] -= s * n0;
@@ -272,7 +268,7 @@ __device__ __forceinline__ void dflux_pair(T g1, typename PairOf<T>::type rinvB,
   out[4] = pfma(pc<P>(EA + pA), dU, pmul(padd(d[4], dp), UB));
 }
 
-template <typename T, int M, int SCHEME>
+template <typename T, int M, int SCHEME, bool BND>
 __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && SCHEME != 2 ? 2 : 1))
 fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, int nitems, int dir,
          int mode, int stage, const double *__restrict__ dtp, int charwise, int fpform) {
@@ -340,7 +336,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
       const int bc = x < 0 ? bclo : bchi;
       if (bc == 0) { xx = x % nd; if (xx < 0) xx += nd; }
       else if (bc == 1) far = true;
-      else if (bc == 2) xx = x < 0 ? 0 : nd - 1;
+      else if (bc == 2 || !BND) xx = x < 0 ? 0 : nd - 1;
       else {   // rare path: the line's t1 is recovered from its state offset
         xx = x < 0 ? -1 - x : 2 * nd - 1 - x;
         const long long T1 = D->qT1;
@@ -350,11 +346,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         else wall = true;
       }
     };
-    // slip-wall ghost: the mirror cell's state with m - 2 (m.k) k/|k|^2, k the face metric
-    // of the boundary face of this line (face -1/2 or nd-1/2)
-    auto load_wall = [&](int x, int xx, T Q[5]) {
-      wall_ghost<T>(qin + qbase + (long long)xx * qsd, qc, fmet + (x < 0 ? 0LL : (long long)nd * fsd), fcs, Q);
-    };
+
     // global loads of one cell (Q, metric vector, 1/J) with the boundary rule applied
     auto fetch = [&](int x, T Q[5], T k[3], T &invJ) {
       if (x >= -G && x < nd + G) {
@@ -369,12 +361,12 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         if (far) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) Q[v] = qb[v];
-        } else if (wall) {
-          load_wall(x, xx, Q);
         } else {
           const T *qp = qin + qsrc + (long long)xx * qsd;
 #pragma unroll
           for (int v = 0; v < 5; ++v) Q[v] = __ldg(qp + v * qc);
+          // slip wall: reflect about the boundary face of this line (face -1/2 or nd-1/2)
+          if (BND && wall) wall_reflect<T>(Q, fmet + (x < 0 ? 0LL : (long long)nd * fsd), fcs);
         }
       } else {   // beyond every stencil that a face of this line uses
 #pragma unroll
@@ -430,12 +422,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         if (far) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) dst[v * kThreads] = qb[v];
-        } else if (wall) {          // a few cells per line end: loaded and reflected in place
-          T Q[5];
-          load_wall(x, xx, Q);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) dst[v * kThreads] = Q[v];
-        } else {
+        } else {   // a wall ghost copies its mirror cell; the reflection is applied when staged
           const T *qp = qin + qsrc + (long long)xx * qsd;
 #pragma unroll
           for (int v = 0; v < 5; ++v) cp_async_el(dst + v * kThreads, qp + v * qc);
@@ -778,30 +765,38 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
       __syncthreads();
       // ---- stage the next chunk's new cell from this thread's staging slots
       if (nextOK) {
+        const int xs = a + S + 4 + tf;
         const T *src = nsb + tid;
-        const T Q[5] = {src[0], src[kThreads], src[2 * kThreads], src[3 * kThreads], src[4 * kThreads]};
+        T Q[5] = {src[0], src[kThreads], src[2 * kThreads], src[3 * kThreads], src[4 * kThreads]};
         const T k[3] = {src[5 * kThreads], src[6 * kThreads], src[7 * kThreads]};
-        stage_cell(a + S + 4 + tf, Q, k, src[8 * kThreads]);
+        if (BND && xs >= nd && xs < nd + G && bchi >= 3) {   // past the high end: slip-wall ghost?
+          int xx;
+          long long qsrc;
+          bool far, wall;
+          bc_source(xs, xx, qsrc, far, wall);
+          if (wall) wall_reflect<T>(Q, fmet + (long long)nd * fsd, fcs);
+        }
+        stage_cell(xs, Q, k, src[8 * kThreads]);
       }
       __syncthreads();
     }
   }
 }
 
-template <typename T, int M, int SCHEME>
+template <typename T, int M, int SCHEME, bool BND>
 cudaError_t launch_one(const SweepLaunch &L, int charwise, int fp, cudaStream_t s) {
   const size_t smem = ((size_t)(kCellFields + kFaceFields) * kRing + (size_t)(kNextFields + kEpiFields) * kThreads) * sizeof(T);
   if (L.nitems <= 0) return cudaSuccess;
-  fp_sweep<T, M, SCHEME><<<L.grid, kThreads, smem, s>>>(L.blocks, L.items, L.nitems, L.dir, L.mode,
+  fp_sweep<T, M, SCHEME, BND><<<L.grid, kThreads, smem, s>>>(L.blocks, L.items, L.nitems, L.dir, L.mode,
                                                       L.stage, L.dt, charwise, fp);
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool BND>
 cudaError_t launch_sweep_t(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
                            cudaStream_t s) {
 #define FPK_CASE(MM, SS) \
-  if (M == MM && scheme == SS) return launch_one<T, MM, SS>(L, charwise, fp, s);
+  if (M == MM && scheme == SS) return launch_one<T, MM, SS, BND>(L, charwise, fp, s);
   FPK_CASE(2, 0) FPK_CASE(4, 0) FPK_CASE(6, 0) FPK_CASE(8, 0)
   FPK_CASE(2, 1) FPK_CASE(4, 1) FPK_CASE(6, 1) FPK_CASE(8, 1)
   FPK_CASE(2, 2) FPK_CASE(4, 2) FPK_CASE(6, 2) FPK_CASE(8, 2)
@@ -811,16 +806,16 @@ cudaError_t launch_sweep_t(const SweepLaunch &L, int M, int scheme, int charwise
 
 // Opt in to the dynamic shared memory of every variant and return the resident
 // CTAs per SM of the requested one.  Called before any launch or graph capture.
-template <typename T>
+template <typename T, bool BND>
 int prepare_t(int M, int scheme) {
   const size_t smem = ((size_t)(kCellFields + kFaceFields) * kRing + (size_t)(kNextFields + kEpiFields) * kThreads) * sizeof(T);
   int nb = 0;
-#define FPK_OCC(MM, SS)                                                                         \
-  {                                                                                             \
-    cudaFuncSetAttribute(fp_sweep<T, MM, SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                         (int)smem);                                                            \
-    if (M == MM && scheme == SS)                                                                \
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fp_sweep<T, MM, SS>, kThreads, smem);   \
+#define FPK_OCC(MM, SS)                                                                              \
+  {                                                                                                  \
+    cudaFuncSetAttribute(fp_sweep<T, MM, SS, BND>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                         (int)smem);                                                                 \
+    if (M == MM && scheme == SS)                                                                     \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fp_sweep<T, MM, SS, BND>, kThreads, smem);   \
   }
   FPK_OCC(2, 0) FPK_OCC(4, 0) FPK_OCC(6, 0) FPK_OCC(8, 0)
   FPK_OCC(2, 1) FPK_OCC(4, 1) FPK_OCC(6, 1) FPK_OCC(8, 1)
