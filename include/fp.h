@@ -50,7 +50,8 @@ typedef enum {
 enum { FP_WENO5_JS = 0, FP_LINEAR_UPWIND5 = 1, FP_WENO7_JS = 2 };  /* reconstruction: Sec. 2.2.2;
                                                                     WENO7 per Remark 2 */
 enum { FP_F64 = 0, FP_F32_MIXED = 1 };                      /* precision of the sweep */
-enum { FP_BC_PERIODIC = 0, FP_BC_FARFIELD = 1, FP_BC_EXTRAP = 2, FP_BC_SLIP_WALL = 3, FP_BC_CUT = 4 };
+enum { FP_BC_PERIODIC = 0, FP_BC_FARFIELD = 1, FP_BC_EXTRAP = 2, FP_BC_SLIP_WALL = 3, FP_BC_CUT = 4,
+       FP_BC_BLOCK = 5 };
 enum { FP_XI = 0, FP_ETA = 1, FP_ZETA = 2 };
 
 typedef struct {
@@ -74,7 +75,12 @@ typedef struct {
                                    itself with the first transverse index t reversed (t = j for
                                    the i direction, t = i for j and k): ghost x' is the mirror
                                    cell on line n_t-1-t, unchanged; lines with
-                                   cut_width <= t < n_t - cut_width are slip wall (the body) */
+                                   cut_width <= t < n_t - cut_width are slip wall (the body);
+                                 FP_BC_BLOCK     another block of a batch (fp_batch_create_linked):
+                                   ghost x' beyond this side is the linked block's cell next to
+                                   its opposite side (x - n or n_linked + x), same transverse
+                                   indices, read at the same RK stage; single-block calls
+                                   (fp_rhs, fp_rk3_step, fp_rhs_noalloc) reject such blocks */
   double gamma;               /* ratio of specific heats (Sec. 2.1 Eq. EOS: 1.4) */
   double q_inf[5];            /* far-field state; also the reference state of the FP32 form */
   int global_lf;              /* 0 = local Lax-Friedrichs speeds (max over the face's stencil),
@@ -164,6 +170,12 @@ const char *fp_status_string(int status);
 void fp_free(fp_ctx *ctx);                 /* NULL-safe; synchronises the device */
 
 /* ---------------- batched multi-block advance ----------------
+   Multi-block grids: a block side with bc FP_BC_BLOCK is linked to another block of the
+   batch by an fp_block_link.  The ghost nodes the caller passes to fp_init_grid for that
+   side must be the linked block's nodes, so that every metric a stencil reaches is the
+   one the unsplit grid would have.  All blocks of a batch advance through the same RK
+   stages together, and a pass never writes the stage state that it reads, so the linked
+   reads need no synchronisation beyond the launch order.
    A batch advances many independent blocks (same precision, scheme, metric order)
    together: one persistent launch per direction pass covers the work of every
    block, the three RK stages are captured once into a CUDA graph, and each call
@@ -173,6 +185,18 @@ void fp_free(fp_ctx *ctx);                 /* NULL-safe; synchronises the device
    keeps the fastest per size class; it may run kernels on the blocks' buffers. */
 int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int autotune,
                     void *stream, fp_batch **out);
+/* Side `side` (0 = low, 1 = high) of direction `dir` of block `a` (index into the batch's
+   block list) takes its ghost cells from block `b`. */
+typedef struct {
+  int a, dir, side, b;
+} fp_block_link;
+/* fp_batch_create with block links.  Every FP_BC_BLOCK side of every block must be linked
+   exactly once, the linked blocks must have the same extents in the two other directions,
+   and no other side may be linked; otherwise FP_ERR_ARG and nothing is created.
+   fp_batch_create is this call with no links. */
+int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_devs,
+                           const fp_block_link *links, int nlinks, int autotune, void *stream,
+                           fp_batch **out);
 /* One RK3 step of size dt on every block (graph replay). */
 int fp_batch_rk3_step(fp_batch *batch, double dt, void *stream);
 /* dqdt for every block (no graph); dqdt_devs[b] has block b's state layout. */

@@ -16,16 +16,20 @@ LIB_PATH = os.path.join(HERE, "libfpgb300.so")
 FP_OK, FP_ERR_ARG, FP_ERR_CUDA, FP_ERR_OOM, FP_ERR_NONFINITE, FP_ERR_TIMEOUT, FP_ERR_UNSUPPORTED = range(7)
 FP_WENO5_JS, FP_LINEAR_UPWIND5, FP_WENO7_JS = 0, 1, 2
 FP_F64, FP_F32_MIXED = 0, 1
-FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP, FP_BC_SLIP_WALL, FP_BC_CUT = 0, 1, 2, 3, 4
+FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP, FP_BC_SLIP_WALL, FP_BC_CUT, FP_BC_BLOCK = 0, 1, 2, 3, 4, 5
 
 # every symbol include/fp.h declares
 EXPORTS = [
     "fp_ghost_width", "fp_node_ghost_width", "fp_init_grid", "fp_rhs", "fp_rhs_noalloc", "fp_rk3_step", "fp_cfl_dt",
     "fp_get_metrics", "fp_get_face_metrics", "fp_get_device_status", "fp_launches_per_rhs",
     "fp_launches_per_step", "fp_get_tile", "fp_set_tile", "fp_last_error", "fp_status_string",
-    "fp_free", "fp_batch_create", "fp_batch_rk3_step", "fp_batch_rhs", "fp_batch_launches_per_step",
+    "fp_free", "fp_batch_create", "fp_batch_create_linked", "fp_batch_rk3_step", "fp_batch_rhs", "fp_batch_launches_per_step",
     "fp_batch_last_error", "fp_batch_free",
 ]
+
+
+class fp_block_link(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int), ("dir", ctypes.c_int), ("side", ctypes.c_int), ("b", ctypes.c_int)]
 
 
 class fp_grid_desc(ctypes.Structure):
@@ -69,6 +73,9 @@ def lib():
         L.fp_free.restype = None
         L.fp_batch_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP), ctypes.c_int,
                                       _VP, ctypes.POINTER(_VP)]
+        L.fp_batch_create_linked.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP),
+                                             ctypes.POINTER(fp_block_link), ctypes.c_int, ctypes.c_int,
+                                             _VP, ctypes.POINTER(_VP)]
         L.fp_batch_rk3_step.argtypes = [_VP, ctypes.c_double, _VP]
         L.fp_batch_rhs.argtypes = [_VP, ctypes.POINTER(_VP), _VP]
         L.fp_batch_launches_per_step.argtypes = [_VP]
@@ -195,6 +202,21 @@ def fp_batch_create(ctxs, q_ptrs, autotune=1, stream=0):
     st = lib().fp_batch_create(arr, n, qs, int(autotune), stream, ctypes.byref(out))
     if st != FP_OK:
         raise FPError(st, "fp_batch_create")
+    return out
+
+
+def fp_batch_create_linked(ctxs, q_ptrs, links, autotune=1, stream=0):
+    """links: iterable of (a, dir, side, b): side `side` of direction `dir` of block a takes
+    its ghost cells from block b."""
+    n = len(ctxs)
+    arr = (_VP * n)(*[c.value if isinstance(c, _VP) else c for c in ctxs])
+    qs = (_VP * n)(*q_ptrs)
+    links = list(links)
+    la = (fp_block_link * max(1, len(links)))(*[fp_block_link(*l) for l in links])
+    out = _VP()
+    st = lib().fp_batch_create_linked(arr, n, qs, la, len(links), int(autotune), stream, ctypes.byref(out))
+    if st != FP_OK:
+        raise FPError(st, "fp_batch_create_linked")
     return out
 
 

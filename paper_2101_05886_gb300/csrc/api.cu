@@ -86,6 +86,14 @@ int bfail(fp_batch *b, int st, const std::string &msg) {
 // separate sweep variant, so blocks without them run a sweep without their code)
 int has_bnd(const fp_grid_desc &d, int dir) { return d.bc[dir][0] >= FP_BC_SLIP_WALL || d.bc[dir][1] >= FP_BC_SLIP_WALL; }
 
+// some side of the block takes its ghosts from another block (batch only)
+int has_link(const fp_grid_desc &d) {
+  for (int k = 0; k < d.dims; ++k)
+    for (int s = 0; s < 2; ++s)
+      if (d.bc[k][s] == FP_BC_BLOCK) return 1;
+  return 0;
+}
+
 int ghost_of(int M, int scheme) { return std::max(scheme == FP_WENO7_JS ? 4 : 3, M / 2); }
 
 int prepare(int is_f32, int M, int scheme) {
@@ -160,6 +168,7 @@ void fill_dirs(fp_ctx *c) {
   B.global_lf = c->desc.global_lf;
   B.lamg = c->lamg;
   B.cut = c->desc.cut_width;
+  for (int d = 0; d < 3; ++d) B.nbr[d][0] = B.nbr[d][1] = -1;
 }
 
 void make_items(const BlockDev &B, int bidx, int d, std::vector<int2> &out) {
@@ -217,7 +226,7 @@ int validate(const fp_grid_desc *d, int ghost_nodes, std::string &why) {
   if (d->global_lf != 0 && d->global_lf != 1) { why = "global_lf must be 0 or 1"; return 0; }
   for (int k = 0; k < d->dims; ++k)
     for (int s = 0; s < 2; ++s)
-      if (d->bc[k][s] < 0 || d->bc[k][s] > FP_BC_CUT) { why = "unknown boundary code"; return 0; }
+      if (d->bc[k][s] < 0 || d->bc[k][s] > FP_BC_BLOCK) { why = "unknown boundary code"; return 0; }
   if (d->cut_width < 0) { why = "cut_width must be non-negative"; return 0; }
   if (!(d->gamma > 1.0) || !std::isfinite(d->gamma)) { why = "gamma must exceed 1"; return 0; }
   const double rho = d->q_inf[0];
@@ -403,6 +412,7 @@ static int run_passes(fp_ctx *c, int rk, cudaStream_t s) {
 int fp_rhs(fp_ctx *c, const void *q, void *dqdt, void *stream) {
   if (!c) return FP_ERR_ARG;
   if (!q || !dqdt) return fail(c, FP_ERR_ARG, "fp_rhs: null buffer");
+  if (has_link(c->desc)) return fail(c, FP_ERR_ARG, "fp_rhs: FP_BC_BLOCK sides need a linked batch");
   cudaStream_t s = (cudaStream_t)stream;
   c->hblk.q[0] = const_cast<void *>(q);
   c->hblk.dqdt = dqdt;
@@ -415,6 +425,7 @@ int fp_rk3_step(fp_ctx *c, void *q, double dt, void *stream) {
   if (!c) return FP_ERR_ARG;
   if (!q) return fail(c, FP_ERR_ARG, "fp_rk3_step: null state");
   if (!std::isfinite(dt)) return fail(c, FP_ERR_ARG, "fp_rk3_step: dt not finite");
+  if (has_link(c->desc)) return fail(c, FP_ERR_ARG, "fp_rk3_step: FP_BC_BLOCK sides need a linked batch");
   cudaStream_t s = (cudaStream_t)stream;
   c->hblk.q[0] = q;
   int st = sync_block(c, s);
@@ -628,11 +639,34 @@ static int batch_autotune(fp_batch *b, cudaStream_t s) {
 
 int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int autotune,
                     void *stream, fp_batch **out) {
+  return fp_batch_create_linked(blocks, nblocks, q_devs, nullptr, 0, autotune, stream, out);
+}
+
+int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_devs,
+                           const fp_block_link *links, int nlinks, int autotune, void *stream,
+                           fp_batch **out) {
   if (!out) return FP_ERR_ARG;
   *out = nullptr;
-  if (!blocks || !q_devs || nblocks < 1) return FP_ERR_ARG;
+  if (!blocks || !q_devs || nblocks < 1 || nlinks < 0 || (nlinks > 0 && !links)) return FP_ERR_ARG;
   for (int k = 0; k < nblocks; ++k)
     if (!blocks[k] || !q_devs[k]) return FP_ERR_ARG;
+  // every FP_BC_BLOCK side linked exactly once, to a block with the same transverse extents
+  std::vector<int> nbr((size_t)nblocks * 6, -1);
+  for (int l = 0; l < nlinks; ++l) {
+    const fp_block_link &L = links[l];
+    if (L.a < 0 || L.a >= nblocks || L.b < 0 || L.b >= nblocks || L.side < 0 || L.side > 1) return FP_ERR_ARG;
+    const fp_grid_desc &da = blocks[L.a]->desc, &db = blocks[L.b]->desc;
+    if (L.dir < 0 || L.dir >= da.dims || da.bc[L.dir][L.side] != FP_BC_BLOCK) return FP_ERR_ARG;
+    for (int e = 0; e < 3; ++e)
+      if (e != L.dir && da.n[e] != db.n[e]) return FP_ERR_ARG;
+    int &slot = nbr[(size_t)L.a * 6 + L.dir * 2 + L.side];
+    if (slot >= 0) return FP_ERR_ARG;
+    slot = L.b;
+  }
+  for (int k = 0; k < nblocks; ++k)
+    for (int d = 0; d < blocks[k]->desc.dims; ++d)
+      for (int sd = 0; sd < 2; ++sd)
+        if (blocks[k]->desc.bc[d][sd] == FP_BC_BLOCK && nbr[(size_t)k * 6 + d * 2 + sd] < 0) return FP_ERR_ARG;
   const fp_grid_desc &d0 = blocks[0]->desc;
   for (int k = 1; k < nblocks; ++k) {
     const fp_grid_desc &d = blocks[k]->desc;
@@ -655,6 +689,8 @@ int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int
     BlockDev B = blocks[k]->hblk;
     B.q[0] = q_devs[k];
     B.dqdt = nullptr;
+    for (int d = 0; d < 3; ++d)
+      for (int sd = 0; sd < 2; ++sd) B.nbr[d][sd] = nbr[(size_t)k * 6 + d * 2 + sd];
     b->hblk.push_back(B);
   }
   cudaError_t e = cudaMalloc(&b->dblk, nblocks * sizeof(BlockDev));
@@ -766,6 +802,7 @@ NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream) {
   if (!c) return FP_ERR_ARG;
   if (!q || !dqdt) return fail(c, FP_ERR_ARG, "fp_rhs_noalloc: null buffer");
+  if (has_link(c->desc)) return fail(c, FP_ERR_ARG, "fp_rhs_noalloc: FP_BC_BLOCK sides need a linked batch");
   const size_t need = (size_t)5 * (size_t)c->ncells * c->esize;
   if (need > kNoAllocScratchBytes) {
     char msg[256];

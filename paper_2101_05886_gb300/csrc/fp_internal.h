@@ -62,6 +62,7 @@ struct BlockDev {
   int global_lf;       // 1: Lax-Friedrichs speeds from lamg instead of the stencil
   void *lamg;          // T [3 directions][3]: max |U - c|grad||, |U|, |U + c|grad|| over the block
   int cut;             // FP_BC_CUT sides: lines t1 < cut or t1 >= nt1 - cut meet across the cut
+  int nbr[3][2];       // FP_BC_BLOCK sides: index of the linked block in the launch's block table
 };
 
 struct SweepLaunch {

@@ -325,26 +325,39 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 
     auto off = [&](int x) -> int { return lbase + (x & wm) * SS; };
 
-    // boundary rule of a cell index x of this line: the source cell xx on the line with
-    // state offset qsrc, or the far-field state (far); `wall` asks for the momentum to be
-    // reflected about the boundary face's normal.  Codes: 0 periodic, 1 far field,
-    // 2 zero gradient, 3 slip wall (mirror cell), 4 C-grid cut (mirror cell on the line
-    // with t1 reversed, wall outside the cut width).
-    auto bc_source = [&](int x, int &xx, long long &qsrc, bool &far, bool &wall) {
-      xx = x; qsrc = qbase; far = false; wall = false;
-      if (x >= 0 && x < nd) return;
-      const int bc = x < 0 ? bclo : bchi;
-      if (bc == 0) { xx = x % nd; if (xx < 0) xx += nd; }
-      else if (bc == 1) far = true;
-      else if (bc == 2 || !BND) xx = x < 0 ? 0 : nd - 1;
-      else {   // rare path: the line's t1 is recovered from its state offset
-        xx = x < 0 ? -1 - x : 2 * nd - 1 - x;
-        const long long T1 = D->qT1;
-        const int n1 = D->nt1, cw = B->cut;
-        const int s1 = (int)((qbase / T1) % n1);
-        if (bc == 4 && (s1 < cw || s1 >= n1 - cw)) qsrc = qbase + (long long)(n1 - 1 - 2 * s1) * T1;
-        else wall = true;
+    // boundary rule of a cell index x of this line: the source cell (its first component
+    // at src, component stride cs), or the far-field state (far); `wall` asks for the
+    // momentum to be reflected about the boundary face's normal.  Codes: 0 periodic, 1 far
+    // field, 2 zero gradient, 3 slip wall (mirror cell), 4 C-grid cut (mirror cell on the line
+    // with t1 reversed, wall outside the cut width), 5 another block of the batch (its cells
+    // next to its opposite side, same transverse indices, same RK stage).
+    auto bc_source = [&](int x, const T *&src, long long &cs, bool &far, bool &wall) {
+      int xx = x;
+      long long qsrc = qbase;
+      cs = qc; far = false; wall = false;
+      if (x < 0 || x >= nd) {
+        const int bc = x < 0 ? bclo : bchi;
+        if (bc == 0) { xx = x % nd; if (xx < 0) xx += nd; }
+        else if (bc == 1) far = true;
+        else if (bc == 2 || !BND) xx = x < 0 ? 0 : nd - 1;
+        else if (bc == 5) {   // rare path: the line's (t1, t2) are recovered from its offset
+          const BlockDev *NB = blocks + B->nbr[dir][x < 0 ? 0 : 1];
+          const DirDev *ND = &NB->dir[dir];
+          const long long s2 = qbase / D->qT2, s1 = (qbase - s2 * D->qT2) / D->qT1;
+          src = static_cast<const T *>(NB->q[stage]) + s1 * ND->qT1 + s2 * ND->qT2 +
+                (long long)(x < 0 ? ND->nd + x : x - nd) * ND->qsd;
+          cs = NB->qc;
+          return;
+        } else {
+          xx = x < 0 ? -1 - x : 2 * nd - 1 - x;
+          const long long T1 = D->qT1;
+          const int n1 = D->nt1, cw = B->cut;
+          const int s1 = (int)((qbase / T1) % n1);
+          if (bc == 4 && (s1 < cw || s1 >= n1 - cw)) qsrc = qbase + (long long)(n1 - 1 - 2 * s1) * T1;
+          else wall = true;
+        }
       }
+      src = qin + qsrc + (long long)xx * qsd;
     };
 
     // global loads of one cell (Q, metric vector, 1/J) with the boundary rule applied
@@ -354,17 +367,16 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 #pragma unroll
         for (int a = 0; a < 3; ++a) k[a] = met[(3LL * dir + a) * mc + mo];
         invJ = met[9LL * mc + mo];
-        int xx;
-        long long qsrc;
+        const T *qp;
+        long long cs;
         bool far, wall;
-        bc_source(x, xx, qsrc, far, wall);
+        bc_source(x, qp, cs, far, wall);
         if (far) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) Q[v] = qb[v];
         } else {
-          const T *qp = qin + qsrc + (long long)xx * qsd;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) Q[v] = __ldg(qp + v * qc);
+          for (int v = 0; v < 5; ++v) Q[v] = __ldg(qp + v * cs);
           // slip wall: reflect about the boundary face of this line (face -1/2 or nd-1/2)
           if (BND && wall) wall_reflect<T>(Q, fmet + (x < 0 ? 0LL : (long long)nd * fsd), fcs);
         }
@@ -415,17 +427,16 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 #pragma unroll
         for (int a = 0; a < 3; ++a) cp_async_el(dst + (5 + a) * kThreads, met + (3LL * dir + a) * mc + mo);
         cp_async_el(dst + 8 * kThreads, met + 9LL * mc + mo);
-        int xx;
-        long long qsrc;
+        const T *qp;
+        long long cs;
         bool far, wall;
-        bc_source(x, xx, qsrc, far, wall);
+        bc_source(x, qp, cs, far, wall);
         if (far) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) dst[v * kThreads] = qb[v];
         } else {   // a wall ghost copies its mirror cell; the reflection is applied when staged
-          const T *qp = qin + qsrc + (long long)xx * qsd;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) cp_async_el(dst + v * kThreads, qp + v * qc);
+          for (int v = 0; v < 5; ++v) cp_async_el(dst + v * kThreads, qp + v * cs);
         }
       } else {
 #pragma unroll
@@ -770,10 +781,10 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         T Q[5] = {src[0], src[kThreads], src[2 * kThreads], src[3 * kThreads], src[4 * kThreads]};
         const T k[3] = {src[5 * kThreads], src[6 * kThreads], src[7 * kThreads]};
         if (BND && xs >= nd && xs < nd + G && bchi >= 3) {   // past the high end: slip-wall ghost?
-          int xx;
-          long long qsrc;
+          const T *qp;
+          long long cs;
           bool far, wall;
-          bc_source(xs, xx, qsrc, far, wall);
+          bc_source(xs, qp, cs, far, wall);
           if (wall) wall_reflect<T>(Q, fmet + (long long)nd * fsd, fcs);
         }
         stage_cell(xs, Q, k, src[8 * kThreads]);

@@ -32,6 +32,7 @@ BC_FARFIELD = 1
 BC_EXTRAP = 2
 BC_SLIP_WALL = 3
 BC_CUT = 4
+BC_BLOCK = 5
 
 
 def ghost_width(metric_order: int, scheme: int = 0) -> int:
@@ -505,3 +506,46 @@ def perturbed_state(grid: Grid, qinf, amp=1e-3, seed=0):
 def random_smooth_state(grid: Grid, qinf, amp=0.05, seed=0):
     """A non-trivial smooth state for parity checks (larger perturbation)."""
     return perturbed_state(grid, qinf, amp=amp, seed=seed)
+
+
+# --------------------------------------------------------------------------
+# Multi-block splits
+# --------------------------------------------------------------------------
+def split_grid(grid: Grid, direction: int, sizes):
+    """Split a block into consecutive blocks of the given extents along `direction`.
+
+    Returns (blocks, links): each block's ghost nodes are the neighbouring blocks' nodes
+    (sliced from the parent, whose own ghosts serve the outer sides); the inner sides get
+    BC_BLOCK and a link (a, direction, side, b); a periodic parent's outer sides are
+    linked around (last block's high side to the first block's low side).  States are
+    split with `split_state`."""
+    assert sum(sizes) == grid.n[direction] and min(sizes) >= 1
+    Gn = grid.Gn
+    ax = grid.nodes.ndim - 1 - direction          # array axis of `direction` in the node array
+    nb = len(sizes)
+    starts = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(int)
+    periodic = grid.bc[direction] == (BC_PERIODIC, BC_PERIODIC)
+    blocks, links = [], []
+    for b, (a0, nloc) in enumerate(zip(starts, sizes)):
+        sl = [slice(None)] * grid.nodes.ndim
+        sl[ax] = slice(a0, a0 + nloc + 2 * Gn)
+        nodes = np.ascontiguousarray(grid.nodes[tuple(sl)])
+        n = list(grid.n)
+        n[direction] = int(nloc)
+        bc = [list(p) for p in grid.bc]
+        if b > 0 or periodic:
+            bc[direction][0] = BC_BLOCK
+            links.append((b, direction, 0, (b - 1) % nb))
+        if b < nb - 1 or periodic:
+            bc[direction][1] = BC_BLOCK
+            links.append((b, direction, 1, (b + 1) % nb))
+        blocks.append(Grid(grid.dims, tuple(n), Gn, nodes, tuple(map(tuple, bc)),
+                           f"{grid.name}_part{b}", grid.cut))
+    return blocks, links
+
+
+def split_state(q: np.ndarray, direction: int, sizes):
+    """Split a state [5][nk][nj][ni] into the parts of `split_grid`."""
+    ax = q.ndim - 1 - direction
+    cuts = np.cumsum(sizes)[:-1]
+    return [np.ascontiguousarray(p) for p in np.split(q, cuts, axis=ax)]

@@ -87,11 +87,12 @@ class Block:
 class Batch:
     """Many blocks advanced together by one CUDA-graph replay per RK step."""
 
-    def __init__(self, blocks, states, autotune=True):
+    def __init__(self, blocks, states, autotune=True, links=()):
+        """links: (a, dir, side, b) tuples for the FP_BC_BLOCK sides (fp_batch_create_linked)."""
         self.blocks = list(blocks)
         self.states = list(states)
-        self.batch = B.fp_batch_create([b.ctx for b in self.blocks], [q.data_ptr() for q in self.states],
-                                       int(autotune), _stream())
+        self.batch = B.fp_batch_create_linked([b.ctx for b in self.blocks], [q.data_ptr() for q in self.states],
+                                              links, int(autotune), _stream())
 
     def rk3_step(self, dt: float):
         B.fp_batch_rk3_step(self.batch, dt, _stream())
