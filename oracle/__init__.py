@@ -57,6 +57,9 @@ def lib():
         L.or_weno7.argtypes = [_D]
         L.or_weno7.restype = ctypes.c_double
         L.or_weno7_parts.argtypes = [_D, _D, _D]
+        L.or_wenocu6.argtypes = [_D]
+        L.or_wenocu6.restype = ctypes.c_double
+        L.or_wenocu6_parts.argtypes = [_D, _D, _D, _D]
         L.or_interp_coef.argtypes = [ctypes.c_int, _D]
         L.or_weno5.argtypes = [_D]
         L.or_weno5.restype = ctypes.c_double
@@ -171,6 +174,20 @@ def weno7_parts(v):
     b = np.zeros(4)
     lib().or_weno7_parts(_p(v), _p(q), _p(b))
     return q, b
+
+
+def wenocu6(v) -> float:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return lib().or_wenocu6(_p(v))
+
+
+def wenocu6_parts(v):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    q = np.zeros(4)
+    b = np.zeros(4)
+    t = np.zeros(1)
+    lib().or_wenocu6_parts(_p(v), _p(q), _p(b), _p(t))
+    return q, b, float(t[0])
 
 
 def lu5(v) -> float:

@@ -147,7 +147,7 @@ static int valid_cfg(const or_cfg *c) {
   if (!c) return 0;
   if (c->dims != 2 && c->dims != 3) return 0;
   if (c->M != 2 && c->M != 4 && c->M != 6 && c->M != 8) return 0;
-  if (c->scheme < 0 || c->scheme > 2) return 0;
+  if (c->scheme < 0 || c->scheme > 3) return 0;
   for (int d = 0; d < 3; ++d) if (c->n[d] < 1) return 0;
   if (c->dims == 2 && c->n[2] != 1) return 0;
   for (int d = 0; d < c->dims; ++d)
@@ -332,6 +332,47 @@ double or_weno7(const double v[7]) {
   for (int k = 0; k < 4; ++k) {
     double t = beta[k] + eps;
     alpha[k] = C7[k] / (t * t);
+    s += alpha[k];
+  }
+  double r = 0.0;
+  for (int k = 0; k < 4; ++k) r += (alpha[k] / s) * q[k];
+  return r;
+}
+
+/* WENOCU6, the sixth-order adaptive central-upwind WENO scheme that Remark 2 names (its
+   formulas are in the cited scheme paper, not here).  Four 3-point sub-stencils over the
+   cells i-2..i+3: the three upwind ones of WENO5 and the downwind {i+1, i+2, i+3}; their
+   parabolic face values q_k; linear weights d = (1, 9, 9, 1)/20, which make the combination
+   the 6-point central face value (1, -8, 37, 37, -8, 1)/60 (the M6 weights of Sec. 3).  The
+   downwind stencil's smoothness indicator is that of the whole 6-point stencil, beta6, the
+   integral definition sum_{l=1..5} int_{cell} h^(2l-1) (p^(l))^2 of its quintic (the quadratic
+   form below is 120960 beta6).  The reference indicator is tau6 = |beta6 - (beta0 + 4 beta1 +
+   beta2)/6| and the weights alpha_k = d_k (C + tau6/(beta_k + eps))^q with C = 20, q = 2,
+   eps = 1e-40. */
+void or_wenocu6_parts(const double v[6], double q[4], double beta[4], double *tau) {
+  double q3[3], b3[3];
+  weno5_parts(v, q3, b3);
+  for (int k = 0; k < 3; ++k) { q[k] = q3[k]; beta[k] = b3[k]; }
+  q[3] = (11.0 * v[3] - 7.0 * v[4] + 2.0 * v[5]) / 6.0;
+  const double *a = v;
+  beta[3] = (a[0] * (271779.0 * a[0] - 2380800.0 * a[1] + 4086352.0 * a[2] - 3462252.0 * a[3] +
+                     1458762.0 * a[4] - 245620.0 * a[5]) +
+             a[1] * (5653317.0 * a[1] - 20427884.0 * a[2] + 17905032.0 * a[3] - 7727988.0 * a[4] +
+                     1325006.0 * a[5]) +
+             a[2] * (19510972.0 * a[2] - 35817664.0 * a[3] + 15929912.0 * a[4] - 2792660.0 * a[5]) +
+             a[3] * (17195652.0 * a[3] - 15880404.0 * a[4] + 2863984.0 * a[5]) +
+             a[4] * (3824847.0 * a[4] - 1429976.0 * a[5]) + 139633.0 * a[5] * a[5]) / 120960.0;
+  *tau = fabs(beta[3] - (beta[0] + 4.0 * beta[1] + beta[2]) / 6.0);
+}
+
+double or_wenocu6(const double v[6]) {
+  static const double D6[4] = {0.05, 0.45, 0.45, 0.05};
+  const double C = 20.0, eps = 1.0e-40;
+  double q[4], beta[4], tau, alpha[4], s = 0.0;
+  or_wenocu6_parts(v, q, beta, &tau);
+  for (int k = 0; k < 4; ++k) {
+    const double t = C + tau / (beta[k] + eps);
+    alpha[k] = D6[k] * t * t;
     s += alpha[k];
   }
   double r = 0.0;
@@ -542,6 +583,11 @@ static void face_flux_impl(const or_cfg *c, const double q8[40], const double me
       for (int t = 0; t < 7; ++t) { vp[t] = fpl[t]; vm[t] = fmi[7 - t]; }   /* i-3..i+3 and i+4..i-2 */
       rp = or_weno7(vp);
       rm = or_weno7(vm);
+    } else if (c->scheme == 3) {
+      double vp[6], vm[6];
+      for (int t = 0; t < 6; ++t) { vp[t] = fpl[t]; vm[t] = fmi[5 - t]; }   /* i-2..i+3 and i+3..i-2 */
+      rp = or_wenocu6(vp);
+      rm = or_wenocu6(vm);
     } else {
       double vp[5] = {fpl[0], fpl[1], fpl[2], fpl[3], fpl[4]};        /* i-2 .. i+2 */
       double vm[5] = {fmi[5], fmi[4], fmi[3], fmi[2], fmi[1]};        /* i+3 .. i-1 */

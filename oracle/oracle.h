@@ -27,7 +27,7 @@ typedef struct {
   int dims;        /* 2 or 3 */
   int n[3];        /* ni, nj, nk (nk = 1 in 2-D) */
   int M;           /* metric and face-interpolation order: 2, 4, 6 or 8 */
-  int scheme;      /* 0 = WENO5-JS, 1 = 5th-order linear upwind, 2 = WENO7-JS */
+  int scheme;      /* 0 = WENO5-JS, 1 = 5th-order linear upwind, 2 = WENO7-JS, 3 = WENOCU6 */
   int fp;          /* 1 = free-stream-preserving form, 0 = plain scheme */
   int charwise;    /* 1 = characteristic-wise (Roe eigenvectors), 0 = component-wise */
   int form;        /* 2 = WENO(F_m - F*_m + F*_face) (Eq. my_point2), 1 = WENO(F_m - F*_m) + F*_face (Eq. my_point1) */
@@ -59,6 +59,8 @@ double or_weno5(const double v[5]);           /* WENO5-JS of v[0..4] = f_{i-2..i
 double or_lu5(const double v[5]);             /* linear upwind 5 = WENO with optimal weights */
 double or_weno7(const double v[7]);           /* WENO7-JS of v[0..6] = f_{i-3..i+3} at i+1/2 */
 void or_weno7_parts(const double v[7], double q[4], double beta[4]);
+double or_wenocu6(const double v[6]);         /* WENOCU6 of v[0..5] = f_{i-2..i+3} at i+1/2 */
+void or_wenocu6_parts(const double v[6], double q[4], double beta[4], double *tau);
 void or_eigensystem(const double qL[5], const double qR[5], const double k[3], double gamma,
                     double L[25], double R[25]);
 int or_metrics(const or_cfg *c, const double *nodes, int Gn, double *met);
