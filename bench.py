@@ -296,8 +296,9 @@ def run_gpu(args):
 
 def run_variants(I, B, Block, Gn, M, torch, stream, nsteps=5):
     """FP32 RK3 steps on one 256^3 wavy block (Mach 0.8 + vortex) for the paper's
-    characteristic WENO5-JS, the linear-upwind scheme, component-wise WENO5-JS and
-    characteristic WENO7-JS (all under the free-stream-preserving form, metric order M)."""
+    characteristic WENO5-JS, the linear-upwind scheme, component-wise WENO5-JS,
+    characteristic WENO7-JS and characteristic WENOCU6 (all under the free-stream-preserving
+    form, metric order M)."""
     Gn = max(Gn, B.fp_node_ghost_width(M, B.FP_WENO7_JS))
     g = I.periodic_wavy_3d((256, 256, 256), L=10.0, amp=0.08, Gn=Gn)
     qinf = I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0)
@@ -305,7 +306,8 @@ def run_variants(I, B, Block, Gn, M, torch, stream, nsteps=5):
     ncell = 256 ** 3
     out = {}
     for name, scheme, charw in (("weno5_char", B.FP_WENO5_JS, 1), ("lu5_char", B.FP_LINEAR_UPWIND5, 1),
-                                ("weno5_comp", B.FP_WENO5_JS, 0), ("weno7_char", B.FP_WENO7_JS, 1)):
+                                ("weno5_comp", B.FP_WENO5_JS, 0), ("weno7_char", B.FP_WENO7_JS, 1),
+                                ("wenocu6_char", B.FP_WENOCU6, 1)):
         blk = Block(g, metric_order=M, scheme=scheme, characteristic=charw, precision=B.FP_F32_MIXED,
                     q_inf=qinf)
         q = blk.to_device(q0)

@@ -47,8 +47,10 @@ typedef enum {
   FP_ERR_UNSUPPORTED = 6   /* valid but not implemented combination */
 } fp_status;
 
-enum { FP_WENO5_JS = 0, FP_LINEAR_UPWIND5 = 1, FP_WENO7_JS = 2 };  /* reconstruction: Sec. 2.2.2;
-                                                                    WENO7 per Remark 2 */
+enum { FP_WENO5_JS = 0, FP_LINEAR_UPWIND5 = 1, FP_WENO7_JS = 2, FP_WENOCU6 = 3 };
+/* reconstruction: WENO5-JS and linear upwind per Sec. 2.2.2; WENO7-JS and WENOCU6 per
+   Remark 2 (WENOCU6: six-point adaptive central-upwind, linear limit the M6 central face
+   value, C = 20, power 2, epsilon 1e-40) */
 enum { FP_F64 = 0, FP_F32_MIXED = 1 };                      /* precision of the sweep */
 enum { FP_BC_PERIODIC = 0, FP_BC_FARFIELD = 1, FP_BC_EXTRAP = 2, FP_BC_SLIP_WALL = 3, FP_BC_CUT = 4,
        FP_BC_BLOCK = 5 };
@@ -59,7 +61,7 @@ typedef struct {
   int n[3];                   /* solution points ni, nj, nk (nk = 1 when dims == 2) */
   int metric_order;           /* M in {2,4,6,8}: order of metrics, Jacobian and every
                                  face interpolation (Sec. 3 Eq. metric_discret, Remark 3) */
-  int scheme;                 /* FP_WENO5_JS, FP_LINEAR_UPWIND5 or FP_WENO7_JS */
+  int scheme;                 /* FP_WENO5_JS, FP_LINEAR_UPWIND5, FP_WENO7_JS or FP_WENOCU6 */
   int free_stream_preserving; /* 1 = the paper's FP face flux, 0 = plain scheme (control) */
   int characteristic;         /* 1 = Roe characteristic-wise splitting (paper), 0 = component-wise */
   int precision;              /* FP_F64, or FP_F32_MIXED: metrics built in FP64, sweep in FP32 */

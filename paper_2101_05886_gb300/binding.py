@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfpgb300.so")
 
 FP_OK, FP_ERR_ARG, FP_ERR_CUDA, FP_ERR_OOM, FP_ERR_NONFINITE, FP_ERR_TIMEOUT, FP_ERR_UNSUPPORTED = range(7)
-FP_WENO5_JS, FP_LINEAR_UPWIND5, FP_WENO7_JS = 0, 1, 2
+FP_WENO5_JS, FP_LINEAR_UPWIND5, FP_WENO7_JS, FP_WENOCU6 = 0, 1, 2, 3
 FP_F64, FP_F32_MIXED = 0, 1
 FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP, FP_BC_SLIP_WALL, FP_BC_CUT, FP_BC_BLOCK = 0, 1, 2, 3, 4, 5
 

@@ -211,7 +211,8 @@ int validate(const fp_grid_desc *d, int ghost_nodes, std::string &why) {
   if (d->dims != 2 && d->dims != 3) { why = "dims must be 2 or 3"; return 0; }
   const int M = d->metric_order;
   if (M != 2 && M != 4 && M != 6 && M != 8) { why = "metric_order must be 2, 4, 6 or 8"; return 0; }
-  if (d->scheme != FP_WENO5_JS && d->scheme != FP_LINEAR_UPWIND5 && d->scheme != FP_WENO7_JS) { why = "unknown scheme"; return 0; }
+  if (d->scheme != FP_WENO5_JS && d->scheme != FP_LINEAR_UPWIND5 && d->scheme != FP_WENO7_JS &&
+      d->scheme != FP_WENOCU6) { why = "unknown scheme"; return 0; }
   const int G = ghost_of(M, d->scheme);
   for (int k = 0; k < 3; ++k) {
     if (d->n[k] < 1) { why = "n must be positive"; return 0; }

@@ -112,6 +112,59 @@ __device__ __forceinline__ typename PairOf<T>::type recon5_pair(
   return pfma(num, pmk(Num<T>::rcp(den.x), Num<T>::rcp(den.y)), v2);
 }
 
+// WENOCU6 (the sixth-order adaptive central-upwind WENO that Remark 2 names) for a pair
+// of six-point stencils i-2..i+3, in the first differences a..e of the six values: the
+// three upwind parabolic sub-stencils of WENO5 and the downwind {i+1, i+2, i+3}, linear
+// weights (1, 9, 9, 1)/20 (the M6 central face value), the downwind stencil judged by the
+// six-point indicator beta6 (integral definition; 120960 beta6 below), reference
+// tau6 = |beta6 - (beta0 + 4 beta1 + beta2)/6|, alpha_k = d_k (20 + tau6/(beta_k + 1e-40))^2.
+// The ratio is capped at 1e18 so that alpha stays finite in FP32; a cap that only binds
+// where a sub-stencil is flat to 1e-18 of tau6.
+template <typename T>
+__device__ __forceinline__ T cu6_ratio(T tau, T beta) {
+  const T r = tau / (beta + T(1.0e-40));
+  return r < T(1.0e18) ? r : T(1.0e18);
+}
+template <typename T>
+__device__ __forceinline__ typename PairOf<T>::type recon6cu_pair(const typename PairOf<T>::type v[6]) {
+  using P = typename PairOf<T>::type;
+  const P a = psub(v[1], v[0]), b = psub(v[2], v[1]), c = psub(v[3], v[2]);
+  const P d = psub(v[4], v[3]), e = psub(v[5], v[4]);
+  // 6 (q_k - v2)
+  const P r0 = pfma(pc<P>(T(5)), b, pmul(pc<P>(T(-2)), a));
+  const P r1 = pfma(pc<P>(T(2)), c, b);
+  const P r2 = pfma(pc<P>(T(4)), c, pmul(pc<P>(T(-1)), d));
+  const P r3 = pfma(pc<P>(T(2)), e, pfma(pc<P>(T(-5)), d, pmul(pc<P>(T(6)), c)));
+  // WENO5 indicators of the three upwind sub-stencils
+  const P d0 = psub(b, a), e0 = pfma(pc<P>(T(3)), b, pmul(pc<P>(T(-1)), a));
+  const P d1 = psub(c, b), e1 = padd(b, c);
+  const P d2 = psub(d, c), e2 = pfma(pc<P>(T(-3)), c, d);
+  const P c13 = pc<P>(T(13.0 / 12.0)), q4 = pc<P>(T(0.25));
+  const P b0 = pfma(c13, pmul(d0, d0), pmul(q4, pmul(e0, e0)));
+  const P b1 = pfma(c13, pmul(d1, d1), pmul(q4, pmul(e1, e1)));
+  const P b2 = pfma(c13, pmul(d2, d2), pmul(q4, pmul(e2, e2)));
+  // 120960 beta6 as a quadratic form of the differences
+  P f = pmul(a, pfma(pc<P>(T(271779)), a, pfma(pc<P>(T(-1837242)), b, pfma(pc<P>(T(2249110)), c,
+             pfma(pc<P>(T(-1213142)), d, pmul(pc<P>(T(245620)), e))))));
+  f = pfma(b, pfma(pc<P>(T(3544296)), b, pfma(pc<P>(T(-9252940)), c, pfma(pc<P>(T(5189840)), d,
+             pmul(pc<P>(T(-1079386)), e)))), f);
+  f = pfma(c, pfma(pc<P>(T(6713736)), c, pfma(pc<P>(T(-7947412)), d, pmul(pc<P>(T(1713274)), e))), f);
+  f = pfma(d, pfma(pc<P>(T(2534504)), d, pmul(pc<P>(T(-1150710)), e)), f);
+  f = pfma(e, pmul(pc<P>(T(139633)), e), f);
+  const P b3 = pmul(f, pc<P>(T(1.0 / 120960.0)));
+  const P tt = psub(b3, pmul(pc<P>(T(1.0 / 6.0)), pfma(pc<P>(T(4)), b1, padd(b0, b2))));
+  const T tx = tt.x < T(0) ? -tt.x : tt.x, ty = tt.y < T(0) ? -tt.y : tt.y;
+  const P w0 = padd(pc<P>(T(20)), pmk(cu6_ratio(tx, b0.x), cu6_ratio(ty, b0.y)));
+  const P w1 = padd(pc<P>(T(20)), pmk(cu6_ratio(tx, b1.x), cu6_ratio(ty, b1.y)));
+  const P w2 = padd(pc<P>(T(20)), pmk(cu6_ratio(tx, b2.x), cu6_ratio(ty, b2.y)));
+  const P w3 = padd(pc<P>(T(20)), pmk(cu6_ratio(tx, b3.x), cu6_ratio(ty, b3.y)));
+  const P a0 = pmul(pc<P>(T(0.05)), pmul(w0, w0)), a1 = pmul(pc<P>(T(0.45)), pmul(w1, w1));
+  const P a2 = pmul(pc<P>(T(0.45)), pmul(w2, w2)), a3 = pmul(pc<P>(T(0.05)), pmul(w3, w3));
+  const P num = pfma(a3, r3, pfma(a2, r2, pfma(a1, r1, pmul(a0, r0))));
+  const P den = pmul(pc<P>(T(6)), padd(padd(a0, a1), padd(a2, a3)));
+  return pfma(num, pmk(Num<T>::rcp(den.x), Num<T>::rcp(den.y)), v[2]);
+}
+
 // Seventh-order WENO-JS (four 4-point sub-stencils, optimal weights (1,12,18,4)/35,
 // smoothness indicators of the integral definition) for a pair of seven-point stencils,
 // written in the first differences d1..d6 of the seven values.
@@ -672,6 +725,12 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
             for (int t = 0; t < 7; ++t) w7[t] = pmk(fpl[t][v], fmi[7 - t][v]);   // i-3..i+3 / i+4..i-2
             const P r = recon7_pair<T>(w7);
             h[v] = r.x + r.y;
+          } else if constexpr (SCHEME == 3) {
+            P w6[6];
+#pragma unroll
+            for (int t = 0; t < 6; ++t) w6[t] = pmk(fpl[t][v], fmi[5 - t][v]);   // i-2..i+3 / i+3..i-2
+            const P r = recon6cu_pair<T>(w6);
+            h[v] = r.x + r.y;
           } else {
             const P r = recon5_pair<T, SCHEME>(pmk(fpl[0][v], fmi[5][v]), pmk(fpl[1][v], fmi[4][v]),
                                                pmk(fpl[2][v], fmi[3][v]), pmk(fpl[3][v], fmi[2][v]),
@@ -811,6 +870,7 @@ cudaError_t launch_sweep_t(const SweepLaunch &L, int M, int scheme, int charwise
   FPK_CASE(2, 0) FPK_CASE(4, 0) FPK_CASE(6, 0) FPK_CASE(8, 0)
   FPK_CASE(2, 1) FPK_CASE(4, 1) FPK_CASE(6, 1) FPK_CASE(8, 1)
   FPK_CASE(2, 2) FPK_CASE(4, 2) FPK_CASE(6, 2) FPK_CASE(8, 2)
+  FPK_CASE(2, 3) FPK_CASE(4, 3) FPK_CASE(6, 3) FPK_CASE(8, 3)
 #undef FPK_CASE
   return cudaErrorInvalidValue;
 }
@@ -831,6 +891,7 @@ int prepare_t(int M, int scheme) {
   FPK_OCC(2, 0) FPK_OCC(4, 0) FPK_OCC(6, 0) FPK_OCC(8, 0)
   FPK_OCC(2, 1) FPK_OCC(4, 1) FPK_OCC(6, 1) FPK_OCC(8, 1)
   FPK_OCC(2, 2) FPK_OCC(4, 2) FPK_OCC(6, 2) FPK_OCC(8, 2)
+  FPK_OCC(2, 3) FPK_OCC(4, 3) FPK_OCC(6, 3) FPK_OCC(8, 3)
 #undef FPK_OCC
   return nb > 0 ? nb : 1;
 }

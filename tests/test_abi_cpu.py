@@ -42,7 +42,7 @@ def test_status_strings(lib):
         assert lib.fp_status_string(st)
 
 
-@pytest.mark.parametrize("field,value", [("dims", 4), ("metric_order", 5), ("scheme", 3), ("precision", 3),
+@pytest.mark.parametrize("field,value", [("dims", 4), ("metric_order", 5), ("scheme", 4), ("precision", 3),
                                          ("gamma", 0.9), ("characteristic", 2), ("free_stream_preserving", -1)])
 def test_invalid_descriptor_is_rejected_before_any_gpu_work(lib, field, value):
     d = B.make_desc(3, (8, 8, 8), metric_order=6)

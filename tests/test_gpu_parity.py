@@ -640,3 +640,86 @@ def test_linked_blocks_are_rejected_outside_a_linked_batch():
               autotune=False, links=[(0, 0, 1, 1)])
     for b in blocks + [whole]:
         b.close()
+
+
+# ---- WENOCU6 under the same free-stream-preserving wrapper (Remark 2) ----
+CU6_CASES = [("2d_vortex", 6, 1, 1), ("3d_vortex", 6, 1, 1), ("3d_vortex", 8, 0, 1), ("3d_vortex", 4, 1, 0),
+             ("3d_ogrid", 6, 1, 1), ("3d_min", 6, 1, 1), ("2d_ragged", 2, 1, 1)]
+
+
+@pytest.mark.parametrize("name,M,charwise,fp", CU6_CASES)
+def test_wenocu6_rhs_parity_fp64(name, M, charwise, fp):
+    """FP64 bound as for WENO7: 1e-12 or twice the oracle's own one-ulp response, whichever
+    is larger.  The WENOCU6 weights have no regularising epsilon (1e-40): where a
+    sub-stencil of the small FP difference values is nearly flat, tau6/beta_k reacts to
+    the last bits of the data, and the residual moves by 1e-7 to 3e-6 under one-ulp input
+    changes on these cases; no two FP64 evaluations can agree more closely than that."""
+    CU = B.FP_WENOCU6
+    g, qinf, q = _case(name, M, CU)
+    blk = Block(g, metric_order=M, scheme=CU, fp=fp, characteristic=charwise, precision=F64, q_inf=qinf)
+    dq = blk.rhs(blk.to_device(q)).cpu().numpy()
+    cfg = O.cfg_for(g, M=M, scheme=CU, fp=fp, charwise=charwise, qinf=qinf)
+    met = O.metrics(cfg, g.nodes, g.Gn)
+    _, dqo = O.rhs(cfg, met, q)
+    tol = max(1e-12, 2.0 * ulp_sensitivity(cfg, met, q))
+    assert tol <= 1e-5
+    errs = rel_err(dq, dqo, per_component=True)
+    assert max(errs) <= tol, (errs, tol)
+    blk.close()
+
+
+@pytest.mark.parametrize("name,M", [("2d_vortex", 6), ("3d_vortex", 6), ("3d_ogrid", 4)])
+def test_wenocu6_rhs_parity_fp32_mixed(name, M):
+    CU = B.FP_WENOCU6
+    g, qinf, q = _case(name, M, CU)
+    q32 = q.astype(np.float32).astype(np.float64)
+    blk = Block(g, metric_order=M, scheme=CU, precision=F32, q_inf=qinf)
+    dq = blk.rhs(blk.to_device(q32)).cpu().numpy()
+    cfg = O.cfg_for(g, M=M, scheme=CU, qinf=qinf)
+    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q32)
+    errs = rel_err(dq, dqo, per_component=True)
+    assert max(errs) <= 1e-5, errs
+    blk.close()
+
+
+@pytest.mark.parametrize("precision", [F64, F32])
+def test_wenocu6_free_stream_and_batch(precision):
+    """Free stream on the jittered wavy Config-1 grid: FP32 drift exactly zero, FP64 at
+    rounding level; a batch of two WENOCU6 blocks equals the blocks stepped one by one."""
+    CU = B.FP_WENOCU6
+    g = I.wavy_sinsin_2d(n=33, amp=0.1, jitter=0.01, seed=1, Gn=O.node_ghost(6))
+    qinf = I.uniform_qinf(0.5, 30.0)
+    blk = Block(g, metric_order=6, scheme=CU, precision=precision, q_inf=qinf)
+    qd = blk.to_device(I.uniform_state(g, qinf))
+    ref = qd.clone()
+    dt = blk.cfl_dt(qd, 0.5)
+    for _ in range(10):
+        blk.rk3_step(qd, dt)
+    torch.cuda.synchronize()
+    drift = (qd - ref).abs().max().item() / np.abs(qinf).max()
+    assert drift == 0.0 if precision == F32 else drift < 1e-13
+    blk.close()
+    Gn = O.node_ghost(6)
+    grids = [I.periodic_wavy_3d((20, 17, 13), L=10.0, amp=0.08, Gn=Gn), I.cylinder_ogrid((24, 18, 10), Lz=3.0, Gn=Gn)]
+    qv = I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0)
+    singles, batched, qs, refs = [], [], [], []
+    for k, gg in enumerate(grids):
+        q = I.random_smooth_state(gg, qv, amp=0.05, seed=30 + k)
+        if precision == F32:
+            q = q.astype(np.float32).astype(np.float64)
+        b1 = Block(gg, metric_order=6, scheme=CU, precision=precision, q_inf=qv)
+        b2 = Block(gg, metric_order=6, scheme=CU, precision=precision, q_inf=qv)
+        singles.append(b1)
+        batched.append(b2)
+        refs.append(b1.to_device(q))
+        qs.append(b2.to_device(q))
+    bat = Batch(batched, qs, autotune=True)
+    bat.rk3_step(1e-3)
+    for b, r in zip(singles, refs):
+        b.rk3_step(r, 1e-3)
+    torch.cuda.synchronize()
+    for a, r in zip(qs, refs):
+        assert torch.equal(a, r)
+    bat.close()
+    for b in singles + batched:
+        b.close()
