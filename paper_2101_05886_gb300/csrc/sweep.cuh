@@ -122,7 +122,8 @@ __device__ __forceinline__ typename PairOf<T>::type recon5_pair(
 // where a sub-stencil is flat to 1e-18 of tau6.
 template <typename T>
 __device__ __forceinline__ T cu6_ratio(T tau, T beta) {
-  const T r = tau / (beta + T(1.0e-40));
+  if (!(tau > T(0))) return T(0);
+  const T r = tau * Num<T>::rcp(beta + T(1.0e-40));   // +inf when the sum is below FP32 range
   return r < T(1.0e18) ? r : T(1.0e18);
 }
 template <typename T>
