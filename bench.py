@@ -116,6 +116,11 @@ def weak_scaling_value(points_per_rank, stages, ms_max, world):
     return world * points_per_rank * stages / (ms_max * 1e-3) / 1e6
 
 
+def pipe_groups_used(pipe):
+    from paper_2101_05886_gb300 import binding as B
+    return B.fp_pipe_groups(pipe.pipe)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -129,7 +134,7 @@ def run_gpu(args):
     import torch
     from paper_2101_05886_gb300 import binding as B
     from paper_2101_05886_gb300 import inputs as I
-    from paper_2101_05886_gb300.solver import Batch, Block
+    from paper_2101_05886_gb300.solver import Batch, Block, Pipe
 
     rank, world, local = _dist()
     torch.cuda.set_device(local)
@@ -190,24 +195,27 @@ def run_gpu(args):
     # ---- end-to-end through the public API with host buffers (pinned), copies inside
     e2e = None
     if not args.no_e2e:
+        # host-resident states (page-locked) advanced through the pipelined public API
+        # (fp_pipe_*): every step copies each block's state in, advances it and copies it back
         hosts = [torch.empty(q.shape, dtype=q.dtype, pin_memory=True) for q in states]
         for h, q in zip(hosts, states):
             h.copy_(q)
         h2d = sum(h.numel() * h.element_size() for h in hosts)
+        pipe = Pipe(blocks, hosts, groups=args.pipe_groups, autotune=True)
+        pipe.rk3_step(dt)                             # warm-up
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.steps):
-            for h, q in zip(hosts, states):
-                q.copy_(h, non_blocking=True)
-            batch.rk3_step(dt)
-            for h, q in zip(hosts, states):
-                h.copy_(q, non_blocking=True)
+            pipe.rk3_step(dt)
         f1.record(stream)
         torch.cuda.synchronize()
         ems = max_over_ranks(f0.elapsed_time(f1), "cuda")
         e2e = {"value": weak_scaling_value(ncells, stages, ems, world), "unit": "Mcell/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+               "api": f"fp_pipe_rk3_step_host, {pipe_groups_used(pipe)} groups, pinned host states"}
+        pipe.close()
+        del hosts
 
     # ---- roofline of the dominant kernel (the sweep; every launch in the graph is one)
     hbm, src = peaks()
@@ -473,6 +481,7 @@ def main():
     ap.add_argument("--c5", type=int, default=1, help="also time the single 100M-point C-grid (1/0)")
     ap.add_argument("--c5-steps", type=int, default=10)
     ap.add_argument("--variants", type=int, default=1, help="also time scheme variants on a 256^3 block (1/0)")
+    ap.add_argument("--pipe-groups", type=int, default=4, help="groups of the pipelined host-state e2e run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -33,6 +33,8 @@
 #ifndef FP_GB300_H
 #define FP_GB300_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -158,6 +160,10 @@ int fp_get_device_status(fp_ctx *ctx, void *stream);
    and must be serialised by the caller.  q_dev, dqdt_dev and the context as in fp_rhs. */
 int fp_rhs_noalloc(fp_ctx *ctx, const void *q_dev, void *dqdt_dev, void *stream);
 
+/* Bytes of one state array of the block: 5 x n_i x n_j x n_k elements of the precision's
+   type (double for FP_F64, float for FP_F32_MIXED); 0 for a NULL context. */
+size_t fp_state_bytes(const fp_ctx *ctx);
+
 /* Number of kernel launches one fp_rhs / fp_rk3_step call queues. */
 int fp_launches_per_rhs(const fp_ctx *ctx);
 int fp_launches_per_step(const fp_ctx *ctx);
@@ -206,6 +212,28 @@ int fp_batch_rhs(fp_batch *batch, void *const *dqdt_devs, void *stream);
 int fp_batch_launches_per_step(const fp_batch *batch);
 const char *fp_batch_last_error(const fp_batch *batch);
 void fp_batch_free(fp_batch *batch);       /* NULL-safe */
+
+/* ---------------- host-resident states, copies overlapped by compute ----------------
+   A pipe advances blocks whose states live in host memory.  It splits the blocks into
+   `ngroups` groups of about equal size, each a batch (as fp_batch_create) with device state
+   buffers and a stream of its own.  One step issues, group by group on the group's stream,
+   the copies of the group's states to the device, the group's RK3 step and the copies back,
+   so the copy engines move one group's states while the SMs advance another.  Host states
+   should be page-locked (cudaHostAlloc / pinned tensors) for the copies to overlap.  The
+   pipe keeps pointers to the contexts (they must outlive it). */
+typedef struct fp_pipe fp_pipe;
+/* q_host[b]: block b's state in host memory (read once to initialise the device copies, and
+   to autotune when autotune is nonzero).  Allocates the device states and the batches. */
+int fp_pipe_create(fp_ctx *const *blocks, int nblocks, const void *const *q_host, int ngroups,
+                   int autotune, fp_pipe **out);
+/* One RK3 step of size dt: q_host[b] is copied in, advanced and copied back, in place.  The
+   work is ordered after earlier work on `stream`, and `stream` waits for all of it; the host
+   states are complete once `stream` is synchronised. */
+int fp_pipe_rk3_step_host(fp_pipe *pipe, void *const *q_host, double dt, void *stream);
+int fp_pipe_groups(const fp_pipe *pipe);
+int fp_pipe_launches_per_step(const fp_pipe *pipe);
+const char *fp_pipe_last_error(const fp_pipe *pipe);
+void fp_pipe_free(fp_pipe *pipe);          /* NULL-safe; synchronises the pipe's streams */
 
 #ifdef __cplusplus
 }

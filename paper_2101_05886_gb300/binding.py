@@ -24,7 +24,8 @@ EXPORTS = [
     "fp_get_metrics", "fp_get_face_metrics", "fp_get_device_status", "fp_launches_per_rhs",
     "fp_launches_per_step", "fp_get_tile", "fp_set_tile", "fp_last_error", "fp_status_string",
     "fp_free", "fp_batch_create", "fp_batch_create_linked", "fp_batch_rk3_step", "fp_batch_rhs", "fp_batch_launches_per_step",
-    "fp_batch_last_error", "fp_batch_free",
+    "fp_batch_last_error", "fp_batch_free", "fp_state_bytes", "fp_pipe_create", "fp_pipe_rk3_step_host",
+    "fp_pipe_groups", "fp_pipe_launches_per_step", "fp_pipe_last_error", "fp_pipe_free",
 ]
 
 
@@ -83,6 +84,17 @@ def lib():
         L.fp_batch_last_error.restype = ctypes.c_char_p
         L.fp_batch_free.argtypes = [_VP]
         L.fp_batch_free.restype = None
+        L.fp_state_bytes.argtypes = [_VP]
+        L.fp_state_bytes.restype = ctypes.c_size_t
+        L.fp_pipe_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP), ctypes.c_int,
+                                     ctypes.c_int, ctypes.POINTER(_VP)]
+        L.fp_pipe_rk3_step_host.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.c_double, _VP]
+        L.fp_pipe_groups.argtypes = [_VP]
+        L.fp_pipe_launches_per_step.argtypes = [_VP]
+        L.fp_pipe_last_error.argtypes = [_VP]
+        L.fp_pipe_last_error.restype = ctypes.c_char_p
+        L.fp_pipe_free.argtypes = [_VP]
+        L.fp_pipe_free.restype = None
         _lib = L
     return _lib
 
@@ -235,3 +247,37 @@ def fp_batch_launches_per_step(batch):
 
 def fp_batch_free(batch):
     lib().fp_batch_free(batch)
+
+
+def fp_state_bytes(ctx):
+    return lib().fp_state_bytes(ctx)
+
+
+def fp_pipe_create(ctxs, q_host_ptrs, ngroups=4, autotune=1):
+    n = len(ctxs)
+    arr = (_VP * n)(*[c.value if isinstance(c, _VP) else c for c in ctxs])
+    qs = (_VP * n)(*q_host_ptrs)
+    out = _VP()
+    st = lib().fp_pipe_create(arr, n, qs, int(ngroups), int(autotune), ctypes.byref(out))
+    if st != FP_OK:
+        raise FPError(st, "fp_pipe_create")
+    return out
+
+
+def fp_pipe_rk3_step_host(pipe, q_host_ptrs, dt, stream=0):
+    qs = (_VP * len(q_host_ptrs))(*q_host_ptrs)
+    st = lib().fp_pipe_rk3_step_host(pipe, qs, float(dt), stream)
+    if st != FP_OK:
+        raise FPError(st, lib().fp_pipe_last_error(pipe).decode())
+
+
+def fp_pipe_groups(pipe):
+    return lib().fp_pipe_groups(pipe)
+
+
+def fp_pipe_launches_per_step(pipe):
+    return lib().fp_pipe_launches_per_step(pipe)
+
+
+def fp_pipe_free(pipe):
+    lib().fp_pipe_free(pipe)

@@ -53,7 +53,8 @@ struct fp_batch {
   int2 *items[3] = {nullptr, nullptr, nullptr};
   int nitems[3] = {0, 0, 0};
   double *dt_dev = nullptr;
-  double dt_host = 0.0;
+  double *dt_host = nullptr;   // page-locked, so the per-step upload is asynchronous
+  cudaEvent_t dt_ready = nullptr;  // the last upload of dt_host has been consumed
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int dims = 3, M = 6, scheme = 0, charwise = 1, fp = 1, is_f32 = 1, global_lf = 0;
@@ -246,6 +247,8 @@ int fp_ghost_width(int metric_order, int scheme) { return ghost_of(metric_order,
 int fp_node_ghost_width(int metric_order, int scheme) {
   return ghost_of(metric_order, scheme) + 3 * (metric_order / 2);
 }
+
+size_t fp_state_bytes(const fp_ctx *c) { return c ? (size_t)5 * (size_t)c->ncells * c->esize : 0; }
 
 const char *fp_status_string(int st) {
   switch (st) {
@@ -535,6 +538,8 @@ void fp_batch_free(fp_batch *b) {
   cudaFree(b->dblk);
   for (int d = 0; d < 3; ++d) cudaFree(b->items[d]);
   cudaFree(b->dt_dev);
+  if (b->dt_host) cudaFreeHost(b->dt_host);
+  if (b->dt_ready) cudaEventDestroy(b->dt_ready);
   cudaFree(b->lam_items);
   delete b;
 }
@@ -696,6 +701,8 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
   }
   cudaError_t e = cudaMalloc(&b->dblk, nblocks * sizeof(BlockDev));
   if (e == cudaSuccess) e = cudaMalloc(&b->dt_dev, sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->dt_host, sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->dt_ready, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->dt_dev, 0, sizeof(double), s);
   if (e != cudaSuccess) { fp_batch_free(b); return FP_ERR_OOM; }
   {
@@ -748,8 +755,13 @@ int fp_batch_rk3_step(fp_batch *b, double dt, void *stream) {
   if (!b) return FP_ERR_ARG;
   if (!std::isfinite(dt)) return bfail(b, FP_ERR_ARG, "dt not finite");
   cudaStream_t s = (cudaStream_t)stream;
-  b->dt_host = dt;
-  cudaError_t e = cudaMemcpyAsync(b->dt_dev, &b->dt_host, sizeof(double), cudaMemcpyHostToDevice, s);
+  // the previous step's upload must have been consumed before the pinned value is reused
+  cudaError_t e = cudaEventSynchronize(b->dt_ready);
+  if (e == cudaSuccess) {
+    *b->dt_host = dt;
+    e = cudaMemcpyAsync(b->dt_dev, b->dt_host, sizeof(double), cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->dt_ready, s);
   if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
   if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
   return FP_OK;

@@ -114,3 +114,34 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Pipe:
+    """Blocks whose states live in host memory (page-locked CPU tensors), advanced with
+    the host<->device copies overlapped by compute (fp_pipe_*): the blocks are split into
+    `groups` batches with a stream each."""
+
+    def __init__(self, blocks, host_states, groups=4, autotune=True):
+        self.blocks = list(blocks)
+        self.host = list(host_states)
+        for b, h in zip(self.blocks, self.host):
+            assert h.device.type == "cpu" and h.is_contiguous() and tuple(h.shape) == b.shape and h.dtype == b.dtype
+        self.pipe = B.fp_pipe_create([b.ctx for b in self.blocks], [h.data_ptr() for h in self.host],
+                                     groups, int(autotune))
+
+    def rk3_step(self, dt: float):
+        B.fp_pipe_rk3_step_host(self.pipe, [h.data_ptr() for h in self.host], dt, _stream())
+
+    def launches_per_step(self):
+        return B.fp_pipe_launches_per_step(self.pipe)
+
+    def close(self):
+        if self.pipe:
+            B.fp_pipe_free(self.pipe)
+            self.pipe = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

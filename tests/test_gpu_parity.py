@@ -723,3 +723,26 @@ def test_wenocu6_free_stream_and_batch(precision):
     bat.close()
     for b in singles + batched:
         b.close()
+
+
+# ---- host-resident states through the pipelined API ----
+def test_pipe_host_states_equal_the_device_batch():
+    """fp_pipe_rk3_step_host (groups of blocks, copies overlapped by compute) gives every
+    block the same state, bit for bit, as a device-resident batch advanced the same way."""
+    grids, qinf, blocks, states = _mini_batch(F32)
+    ref = [q.clone() for q in states]
+    hosts = [q.cpu().pin_memory() for q in states]
+    from paper_2101_05886_gb300.solver import Pipe
+    pipe = Pipe(blocks, hosts, groups=3, autotune=True)
+    assert B.fp_pipe_groups(pipe.pipe) == 3
+    bat = Batch(blocks, ref, autotune=False)
+    for _ in range(3):
+        pipe.rk3_step(1e-3)
+        bat.rk3_step(1e-3)
+    torch.cuda.synchronize()
+    for h, r in zip(hosts, ref):
+        assert torch.equal(h, r.cpu())
+    pipe.close()
+    bat.close()
+    for b in blocks:
+        b.close()
