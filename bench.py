@@ -116,6 +116,17 @@ def weak_scaling_value(points_per_rank, stages, ms_max, world):
     return world * points_per_rank * stages / (ms_max * 1e-3) / 1e6
 
 
+def relative_error(a, b, floor_frac=0.1):
+    """Largest per-component max |a - b| / max(max |b_c|, 10 % of the largest component's max),
+    the parity metric of the tests, on device tensors [5, ...]."""
+    tau = floor_frac * b.abs().max().item()
+    e = 0.0
+    for c in range(b.shape[0]):
+        scale = max(b[c].abs().max().item(), tau)
+        e = max(e, (a[c] - b[c]).abs().max().item() / scale if scale > 0 else 0.0)
+    return e
+
+
 def pipe_groups_used(pipe):
     from paper_2101_05886_gb300 import binding as B
     return B.fp_pipe_groups(pipe.pipe)
@@ -148,11 +159,14 @@ def run_gpu(args):
     sizes = I.batched_block_sizes(64, 32, 128, 4)[:args.blocks]
     rng = np.random.default_rng(1004)
     blocks, states = [], []
+    grid0 = None
     for k, n in enumerate(sizes):
         g = (I.cylinder_ogrid(n, Lz=float(rng.uniform(1.0, 8.0)), Gn=Gn) if k < 32
              else I.periodic_wavy_3d(n, L=10.0, amp=0.08, Gn=Gn))
         blk = Block(g, metric_order=M, precision=prec, q_inf=qinf)
         q = blk.to_device(I.perturbed_state(g, qinf, amp=1e-3, seed=k))
+        if k == 0:
+            grid0 = g
         blk.grid = None
         blocks.append(blk)
         states.append(q)
@@ -234,12 +248,33 @@ def run_gpu(args):
                     "frac": round(achieved_gbs / hbm, 4), "peak_source": src,
                     "algorithmic_bytes_per_point_stage": round(BYTES_PER_CELL_STAGE_F32, 1)}}
 
+    # ---- the FP32 residual's error against the FP64 sweep (itself within 1e-12 of the FP64
+    # oracle in the parity tests), on block 0 of the workload at its current state
+    err32 = None
+    if rank == 0:
+        b64 = Block(grid0, metric_order=M, precision=B.FP_F64, q_inf=qinf)
+        q32 = states[0]
+        r32 = blocks[0].rhs(q32).double()
+        r64 = b64.rhs(q32.double())
+        err32 = {"case": f"block 0 of the workload ({'x'.join(map(str, sizes[0]))} cylinder O-grid), "
+                         "dQ/dt after the timed steps",
+                 "max_rel": relative_error(r32, r64), "bound": 3e-5}
+        b64.close()
+        del r32, r64
+    grid0 = None
+
     # ---- FP64 plain single block (256^3 wavy grid + vortex) on the same GPU
     fp64 = None
     if not args.no_fp64 and rank == 0:
         g = I.periodic_wavy_3d((256, 256, 256), L=10.0, amp=0.08, Gn=Gn)
         b64 = Block(g, metric_order=M, precision=B.FP_F64, q_inf=I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0))
         q64 = b64.to_device(I.vortex_3d(g, mach=0.8, eps=5.0, L=10.0))
+        # FP32 sweep on the same grid and (float-rounded) state: its residual error
+        b32 = Block(g, metric_order=M, precision=B.FP_F32_MIXED, q_inf=I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0))
+        qr = q64.float()
+        vortex_err = relative_error(b32.rhs(qr).double(), b64.rhs(qr.double()))
+        b32.close()
+        del qr
         del g
         dt64 = b64.cfl_dt(q64, 0.5)
         b64.rk3_step(q64, dt64)
@@ -253,6 +288,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         ms64 = h0.elapsed_time(h1)
         fp64 = {"workload": "single block 256^3 wavy grid, Mach 0.8 + vortex, WENO5-JS FP, M6",
+                "fp32_rhs_max_rel_error_vs_fp64": vortex_err,
                 "value": 256 ** 3 * 3 * n64 / (ms64 * 1e-3) / 1e6, "unit": "Mcell/s",
                 "ms_per_step": ms64 / n64, "dtype": "f64"}
         b64.close()
@@ -293,6 +329,7 @@ def run_gpu(args):
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "roofline": roof, "cpu_baseline": cpu, "fp64_plain_single_block": fp64,
             "c5_single_large": c5, "variants_256cubed_f32": variants, "c4_slip_walls": walls,
+            "fp32_error_vs_fp64": err32,
         }
         print(json.dumps(result))
     for b in blocks:
