@@ -746,3 +746,71 @@ def test_pipe_host_states_equal_the_device_batch():
     bat.close()
     for b in blocks:
         b.close()
+
+
+# ---- full-size parity in the benchmark's launch configuration ----
+def _full_scale(dq):
+    s = dq.abs().amax(dim=(1, 2, 3)).cpu().numpy()
+    return np.maximum(s, 1e-1 * s.max())
+
+
+def test_full_size_batched_workload_sampled_parity():
+    """The 64-block batched workload at full size (34.5M points), in the launch configuration
+    the benchmark times (autotuned tiles, one persistent launch per pass over all blocks):
+    dQ/dt of sampled blocks against the oracle on interior sub-boxes.  FP32 on a Mach 3
+    stream with a 1e-3 perturbation: bound 3e-5 of each block's residual scale."""
+    M = 6
+    Gn = O.node_ghost(M)
+    qinf = I.uniform_qinf(3.0, 0.0)
+    sizes = I.batched_block_sizes(64, 32, 128, 4)
+    rng = np.random.default_rng(1004)
+    sample = (0, 7, 19, 33, 45, 60)
+    keep, blocks, states = {}, [], []
+    for k, n in enumerate(sizes):
+        g = (I.cylinder_ogrid(n, Lz=float(rng.uniform(1.0, 8.0)), Gn=Gn) if k < 32
+             else I.periodic_wavy_3d(n, L=10.0, amp=0.08, Gn=Gn))
+        q = I.perturbed_state(g, qinf, amp=1e-3, seed=k).astype(np.float32).astype(np.float64)
+        blk = Block(g, metric_order=M, precision=F32, q_inf=qinf)
+        states.append(blk.to_device(q))
+        blocks.append(blk)
+        if k in sample:
+            keep[k] = (g, q)
+    bat = Batch(blocks, states, autotune=True)
+    outs = bat.rhs([torch.empty_like(s) for s in states])
+    torch.cuda.synchronize()
+    G = O.ghost(M)
+    for k in sample:
+        g, q = keep[k]
+        n = np.array(sizes[k])
+        scale = _full_scale(outs[k])
+        for lo in (np.array([G, G, G]), (n - 6) // 2, n - 6 - G):
+            ref = oracle_subbox_dqdt(g, q, M, lo, np.array((6, 6, 6)), qinf=qinf)
+            got = outs[k][:, lo[2]:lo[2] + 6, lo[1]:lo[1] + 6, lo[0]:lo[0] + 6].cpu().numpy()
+            err = max(np.abs(got[c] - ref[c]).max() / scale[c] for c in range(5))
+            assert err <= 3e-5, (k, lo, err)
+    bat.close()
+    for b in blocks:
+        b.close()
+
+
+def test_full_size_cgrid_sampled_parity():
+    """The 512 x 384 x 512 C-grid (100.7M points, slip wall + wake cut) at full size, FP32, a
+    1e-2 perturbation of the Mach 0.84 stream: dQ/dt against the oracle on interior
+    sub-boxes next to the wall, in the wake behind the trailing edge and in the field."""
+    M = 6
+    g = I.cgrid_wing(n=(512, 384, 512), Gn=O.node_ghost(M))
+    qinf = I.uniform_qinf(0.84, 3.0)
+    q = I.perturbed_state(g, qinf, amp=1e-2, seed=5).astype(np.float32)
+    blk = Block(g, metric_order=M, precision=F32, q_inf=qinf)
+    dq = blk.rhs(blk.to_device(q))
+    torch.cuda.synchronize()
+    scale = _full_scale(dq)
+    q = q.astype(np.float64)
+    G = O.ghost(M)
+    for lo in ((256, G, 200), (g.cut - 3, 20, 100), (300, 200, 400)):
+        lo = np.array(lo)
+        ref = oracle_subbox_dqdt(g, q, M, lo, np.array((6, 6, 6)), qinf=qinf)
+        got = dq[:, lo[2]:lo[2] + 6, lo[1]:lo[1] + 6, lo[0]:lo[0] + 6].cpu().numpy()
+        err = max(np.abs(got[c] - ref[c]).max() / scale[c] for c in range(5))
+        assert err <= 1e-5, (lo, err)
+    blk.close()
