@@ -534,11 +534,14 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     if (lineOK) {
       if (tf - 1 < nd) prefetch_face(tf - 1, 0);
       cp_async_commit();
-      for (int j = tf; j < S + 8; j += S) {
-        T Q[5], k[3], ij;
-        fetch(-5 + j, Q, k, ij);
-        stage_cell(-5 + j, Q, k, ij);
-      }
+      // S >= 8, so the window's S + 8 cells are one per thread plus a second one for the
+      // threads tf < 8: both loads are issued before either cell is staged
+      const bool two = tf < 8;
+      T Qa[5], ka[3], ija, Qb[5], kb[3], ijb;
+      fetch(-5 + tf, Qa, ka, ija);
+      if (two) fetch(-5 + tf + S, Qb, kb, ijb);
+      stage_cell(-5 + tf, Qa, ka, ija);
+      if (two) stage_cell(-5 + tf + S, Qb, kb, ijb);
     }
     cp_async_wait_all();
     __syncthreads();
