@@ -81,3 +81,18 @@ def test_other_invalid_arguments(lib):
     assert lib.fp_batch_create(None, 0, None, 0, None, ctypes.byref(bo)) == B.FP_ERR_ARG
     lib.fp_free(None)
     lib.fp_batch_free(None)
+
+
+def test_pipe_and_link_calls_reject_null_arguments(lib):
+    """The pipe and linked-batch entry points reject missing arguments before any GPU work."""
+    out = ctypes.c_void_p()
+    assert lib.fp_state_bytes(None) == 0
+    assert lib.fp_pipe_create(None, 1, None, 4, 0, ctypes.byref(out)) == B.FP_ERR_ARG
+    assert lib.fp_pipe_create(None, 0, None, 4, 0, None) == B.FP_ERR_ARG
+    assert lib.fp_pipe_rk3_step_host(None, None, 1e-3, None) == B.FP_ERR_ARG
+    assert lib.fp_pipe_groups(None) == 0
+    assert lib.fp_pipe_launches_per_step(None) == 0
+    lib.fp_pipe_free(None)
+    links = (B.fp_block_link * 1)(B.fp_block_link(0, 0, 1, 0))
+    assert lib.fp_batch_create_linked(None, 1, None, links, 1, 0, None, ctypes.byref(out)) == B.FP_ERR_ARG
+    assert lib.fp_batch_create_linked(None, 1, None, None, 1, 0, None, ctypes.byref(out)) == B.FP_ERR_ARG
