@@ -508,21 +508,30 @@ WALL_CUT_CASES = [
     ("channel_walls_T", 6, 0, F64, 1e-12), ("ogrid_wall", 6, 0, F64, 1e-12), ("ogrid_wall", 4, 0, F32, 3e-5),
     ("parabolic_cut", 6, 0, F64, 1e-12), ("parabolic_cut", 6, 1, F32, 1e-5), ("parabolic_plate", 4, 0, F64, 1e-12),
     ("cgrid_wing", 6, 0, F64, 1e-12), ("cgrid_wing", 6, 0, F32, 1e-5),
+    # the boundary rules combined with the other options of the sweep
+    ("ogrid_wall", 6, 0, F64, 1e-12, 1), ("parabolic_cut", 6, 0, F32, 1e-5, 1), ("cgrid_wing", 4, 1, F64, 1e-12, 1),
+    ("parabolic_cut", 6, 3, F64, None), ("cgrid_wing", 6, 2, F64, None), ("ogrid_wall", 6, 3, F32, 3e-5),
 ]
 
 
-@pytest.mark.parametrize("name,M,scheme,precision,tol", WALL_CUT_CASES)
-def test_wall_and_cut_parity(name, M, scheme, precision, tol):
+@pytest.mark.parametrize("case", WALL_CUT_CASES, ids=lambda c: "-".join(map(str, c)))
+def test_wall_and_cut_parity(case):
+    """Slip walls and C-grid cuts against the oracle.  Case: (grid, M, scheme, precision,
+    tolerance[, global LF]); a tolerance of None takes the conditioning bound of the
+    seven-point and WENOCU6 reconstructions in FP64."""
+    name, M, scheme, precision, tol = case[:5]
+    glf = case[5] if len(case) > 5 else 0
     g, qinf, q = _wall_cut_case(name, M, scheme)
     if precision == F32:
         q = q.astype(np.float32).astype(np.float64)
-    blk = Block(g, metric_order=M, scheme=scheme, precision=precision, q_inf=qinf)
+    blk = Block(g, metric_order=M, scheme=scheme, precision=precision, q_inf=qinf, global_lf=glf)
     dq = blk.rhs(blk.to_device(q)).cpu().numpy()
-    cfg = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf)
+    cfg = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf, global_lf=glf)
     met = O.metrics(cfg, g.nodes, g.Gn)
     _, dqo = O.rhs(cfg, met, q)
-    if tol is None:                              # WENO7 in FP64: the conditioning bound
+    if tol is None:                              # WENO7 / WENOCU6 in FP64: the conditioning bound
         tol = _weno7_tol(cfg, met, q)
+        assert tol <= 1e-5
     errs = rel_err(dq, dqo, per_component=True)
     assert max(errs) <= tol, (errs, tol)
     blk.close()
