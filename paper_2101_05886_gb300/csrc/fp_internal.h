@@ -45,7 +45,9 @@ struct DirDev {
   const void *dk;      // T [3][cells]: k_{i+1/2} - k_{i-1/2} along this direction (FP64-formed)
 };
 
-struct BlockDev {
+// 16-byte aligned and padded so that the sweep can copy a descriptor into shared memory in
+// 16-byte cp.async pieces
+struct alignas(16) BlockDev {
   DirDev dir[3];
   int dims;
   int G;               // metric ghost width

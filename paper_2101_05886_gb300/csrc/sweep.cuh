@@ -226,6 +226,14 @@ __device__ __forceinline__ void cp_async_el(T *smem, const T *gmem) {
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -341,11 +349,39 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
   T *const nsb = fr + kFaceFields * kRing;                  // next chunk's cell, per thread: 9 x 256
   T *const epb = nsb + kNextFields * kThreads;              // epilogue operands, per thread: 16 x 256
   const int tid = threadIdx.x;
+  // Work-item descriptors in shared memory, double-buffered: during an item's first chunk
+  // the next item's (block, first line) and its whole block descriptor are copied in with
+  // cp.async, so an item starts without a chain of dependent global loads, and the chunk
+  // loop reads buffer pointers from here rather than through an L1 that the streamed cells
+  // keep evicting.
+  static_assert(sizeof(BlockDev) % 16 == 0, "descriptor copied in 16-byte pieces");
+  constexpr int kDescPieces = (int)(sizeof(BlockDev) / 16);
+  static_assert(kDescPieces <= kThreads, "one piece per thread");
+  __shared__ __align__(16) unsigned char s_desc[2][sizeof(BlockDev)];
+  __shared__ __align__(16) int2 s_item[2];
+  __shared__ T s_dt;
+  auto fetch_desc = [&](int buf, int blk) {
+    if (tid < kDescPieces)
+      cp_async16(s_desc[buf] + 16 * tid, reinterpret_cast<const unsigned char *>(blocks + blk) + 16 * tid);
+  };
+  if (blockIdx.x < nitems) {            // the first item's descriptor, loaded before the loop
+    if (tid == 0) s_item[0] = items[blockIdx.x];
+    __syncthreads();
+    fetch_desc(0, s_item[0].x);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+  }
 
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const int2 item = items[it];
-    const BlockDev *B = blocks + item.x;
+  int cur = 0;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x, cur ^= 1) {
+    const int2 item = s_item[cur];
+    const BlockDev *B = reinterpret_cast<const BlockDev *>(s_desc[cur]);
     const DirDev *D = &B->dir[dir];
+    const int nit = it + gridDim.x;
+    // the next item's (block, first line): lands by this item's prologue barrier
+    if (tid == 0 && nit < nitems) cp_async8(&s_item[cur ^ 1], items + nit);
+    if (tid == 0) s_dt = mode == MODE_RK ? T(*dtp) : T(0);   // read after the prologue's barrier
     const int S = D->S, TT = D->TT, W = 2 * S;
     // thread roles: along-line index tf and line index tl.  The xi pass puts
     // consecutive threads along the line (coalesced, i contiguous), the other passes
@@ -553,6 +589,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
       if (lineOK && a + tf >= 0 && a + tf < nd) prefetch_epilogue(a + tf);
       if (nextOK) prefetch_cell(a + S + 4 + tf);
       if (nextOK && a + S + tf < nd) prefetch_face(a + S + tf, (ch + 1) & 1);
+      if (ch == 0 && nit < nitems) fetch_desc(cur ^ 1, s_item[cur ^ 1].x);   // next item's descriptor
       cp_async_commit();
       // ---- one face per thread: face ff + 1/2 between cells ff and ff+1
       const int ff = a + tf;
@@ -824,7 +861,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           } else {
             // SSP-RK3 stage (Gottlieb & Shu) in increment form:
             // Q^(s+1) = Q^(s) + a_s (Q^n - Q^(s)) + b_s dt L(Q^(s))
-            const T dt = T(*dtp);
+            const T dt = s_dt;
             const T as = stage == 0 ? T(0) : (stage == 1 ? T(0.75) : T(1.0 / 3.0));
             const T bs = stage == 0 ? T(1) : (stage == 1 ? T(0.25) : T(2.0 / 3.0));
             T *qo_p = static_cast<T *>(B->q[(stage + 1) % 3]) + qo;
