@@ -348,7 +348,9 @@ double or_weno7(const double v[7]) {
    integral definition sum_{l=1..5} int_{cell} h^(2l-1) (p^(l))^2 of its quintic (the quadratic
    form below is 120960 beta6).  The reference indicator is tau6 = |beta6 - (beta0 + 4 beta1 +
    beta2)/6| and the weights alpha_k = d_k (C + tau6/(beta_k + eps))^q with C = 20, q = 2,
-   eps = 1e-40. */
+   eps = 1e-40.  Parity unpinned for C, q and eps (taken from the cited scheme paper, which is
+   not at hand): the pins cover the sub-stencils, the linear weights, beta6 and the scheme's
+   order, and hold for any C, q and eps. */
 void or_wenocu6_parts(const double v[6], double q[4], double beta[4], double *tau) {
   double q3[3], b3[3];
   weno5_parts(v, q3, b3);

@@ -9,6 +9,11 @@
  * table or helper with the CUDA library; the two are compared on the same seeded
  * inputs.
  *
+ * Pins: every function is checked against values the paper prints, closed forms,
+ * invariants or brute force (tests/test_oracle_pins.py), with one exception: parity
+ * unpinned for the constants C = 20, q = 2, eps = 1e-40 of or_wenocu6, which come from
+ * the cited WENOCU6 paper (not at hand); its other parts are pinned.
+ *
  * Layouts (all C order, i fastest, float64):
  *   nodes : [dims][nk+2Gn][nj+2Gn][ni+2Gn]   (2-D: [2][nj+2Gn][ni+2Gn])
  *   met   : [10][nk+2G][nj+2G][ni+2G]         (2-D: [10][1][nj+2G][ni+2G])
