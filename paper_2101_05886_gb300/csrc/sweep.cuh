@@ -360,6 +360,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
   __shared__ __align__(16) unsigned char s_desc[2][sizeof(BlockDev)];
   __shared__ __align__(16) int2 s_item[2];
   __shared__ T s_dt;
+  __shared__ T s_lam[3];                // global Lax-Friedrichs speeds of this item's direction
   auto fetch_desc = [&](int buf, int blk) {
     if (tid < kDescPieces)
       cp_async16(s_desc[buf] + 16 * tid, reinterpret_cast<const unsigned char *>(blocks + blk) + 16 * tid);
@@ -381,7 +382,11 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     const int nit = it + gridDim.x;
     // the next item's (block, first line): lands by this item's prologue barrier
     if (tid == 0 && nit < nitems) cp_async8(&s_item[cur ^ 1], items + nit);
-    if (tid == 0) s_dt = mode == MODE_RK ? T(*dtp) : T(0);   // read after the prologue's barrier
+    if (tid == 0) {                      // read after the prologue's barrier
+      s_dt = mode == MODE_RK ? T(*dtp) : T(0);
+      if (B->global_lf)
+        for (int c = 0; c < 3; ++c) s_lam[c] = static_cast<const T *>(B->lamg)[3 * dir + c];
+    }
     const int S = D->S, TT = D->TT, W = 2 * S;
     // thread roles: along-line index tf and line index tl.  The xi pass puts
     // consecutive threads along the line (coalesced, i contiguous), the other passes
@@ -409,7 +414,6 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     const T *__restrict__ qin = static_cast<const T *>(B->q[stage]);
     const T g1 = T(B->gamma - 1.0), gam = T(B->gamma);
     const int glf = B->global_lf;
-    const T *lamg = glf ? static_cast<const T *>(B->lamg) + 3 * dir : nullptr;
     T qb[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qb[v] = T(B->qbar[v]);
@@ -635,7 +639,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         // Lax-Friedrichs speeds: local (max over the stencil cells i-2..i+3) or global
         T lm = T(0), l0 = T(0), lp = T(0);
         if (glf) {
-          lm = lamg[0]; l0 = lamg[1]; lp = lamg[2];
+          lm = s_lam[0]; l0 = s_lam[1]; lp = s_lam[2];
         } else {
 #pragma unroll
           for (int q = Q0; q < Q0 + NS; ++q) {
