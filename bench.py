@@ -44,8 +44,8 @@ FLOPS_PER_POINT_PASS_F32 = 2280.0
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch measured by ncu for the current kernel (16-block capture, mean of the
-# three passes 95.5 B per point per pass), scaled to a launch over the 64-block workload.
-TRAFFIC_BYTES_PER_POINT_PASS = 95.5
+# three passes 95.4 B per point per pass), scaled to a launch over the 64-block workload.
+TRAFFIC_BYTES_PER_POINT_PASS = 95.4
 
 
 def _dist():
