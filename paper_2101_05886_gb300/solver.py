@@ -27,7 +27,12 @@ class Block:
         self.desc = B.make_desc(grid.dims, grid.n, metric_order, scheme, fp, characteristic,
                                 precision, grid.bc, gamma, q_inf, global_lf, getattr(grid, "cut", 0))
         nodes = np.ascontiguousarray(grid.nodes, dtype=np.float64)
-        self.ctx = B.fp_init_grid(self.desc, nodes.ctypes.data, int(grid.Gn), _stream())
+        ni, nj, nk = self.n
+        gn = int(grid.Gn)
+        want = (2, nj + 2 * gn, ni + 2 * gn) if grid.dims == 2 else (3, nk + 2 * gn, nj + 2 * gn, ni + 2 * gn)
+        if nodes.shape != want:   # the C call reads exactly this many values
+            raise ValueError(f"node array of shape {nodes.shape}, expected {want} for n={self.n}, Gn={gn}")
+        self.ctx = B.fp_init_grid(self.desc, nodes.ctypes.data, gn, _stream())
         self.G = B.fp_ghost_width(metric_order, scheme)
 
     @property
