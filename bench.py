@@ -31,7 +31,7 @@ CLOCK_Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active
            "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
            "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-# Algorithmic bytes per interior point per RK stage of the FP32 form (see DESIGN.md):
+# Algorithmic bytes per interior point per RK stage of the FP32 form:
 # state: read Q^(s) 20 + read Q^n (stages 2,3 only: 2/3 * 20) + write Q^(s+1) 20;
 # cell metrics 9 + 1/J as float 40; face metrics 3 directions x 3 floats 36; per-point
 # face-metric differences 3 directions x 3 floats 36.
@@ -39,7 +39,7 @@ BYTES_PER_CELL_STAGE_F32 = 20 + 20 * 2.0 / 3.0 + 20 + 40 + 36 + 36
 BYTES_PER_CELL_STAGE_F64 = 2 * BYTES_PER_CELL_STAGE_F32
 # FP32 floating-point operations per point per direction pass of the WENO5-JS FP sweep
 # (FFMA counted as 2), counted by ncu on the 16-block subset of the workload
-# (profiles/fp_sweep_f32_batched16_full.md).  The pass is bound by FP32 issue.
+# (an ncu capture of the FP32 sweep).  The pass is bound by FP32 instruction issue.
 FLOPS_PER_POINT_PASS_F32 = 2280.0
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -241,7 +241,7 @@ def run_gpu(args):
     roof = {"bound": "alu", "achieved": round(achieved_tf, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
             "unit": "TFLOP/s", "frac": round(achieved_tf / FP32_PEAK_TFLOPS, 4),
             "traffic": round(TRAFFIC_BYTES_PER_POINT_PASS * ncells) if args.blocks == 64 else None,
-            "peak_source": "FP32 unit count x 2.07 GHz (see DESIGN.md)",
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)",
             "kernel": "fpk::fp_sweep<float,6,0>", "launch_ms": round(per_launch_ms, 4),
             "algorithmic_flops_per_launch": flops_per_launch,
             "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm, "unit": "GB/s",
