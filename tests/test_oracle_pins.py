@@ -347,12 +347,15 @@ def test_my_point1_and_my_point2_forms_agree():
     assert np.abs(R[1] - R[2]).max() / scale.min() < 1e-12
 
 
-def test_appendix_fp_linear_upwind_equals_central_plus_reformulated_dissipation():
+@pytest.mark.parametrize("charwise", [1, 0])
+def test_appendix_fp_linear_upwind_equals_central_plus_reformulated_dissipation(charwise):
     """Sec. 3.1 Eq. (final_form_linear_upwind), first line, with M6 metrics: the FP
     linear-upwind face flux is the 6th-order central flux of F~ plus the 5th-order
-    dissipation of (Q~ - Q*/J) in characteristic space (F^ of Eq. WENO_hatF is zero)."""
+    dissipation of (Q~ - Q*/J) in characteristic space (F^ of Eq. WENO_hatF is zero).
+    Component-wise splitting (charwise = 0) is the same with one speed, the largest
+    |U -+ c|grad|| over the stencil, for every component and no projection."""
     rng = np.random.default_rng(11)
-    cfg = O.make_cfg(3, (8, 8, 8), M=6, scheme=1, fp=1)
+    cfg = O.make_cfg(3, (8, 8, 8), M=6, scheme=1, fp=1, charwise=charwise)
     c6 = np.array([1, -8, 37, 37, -8, 1]) / 60.0
     d5 = np.array([1, -5, 10, -10, 5, -1]) / 60.0
     for _ in range(20):
@@ -386,7 +389,10 @@ def test_appendix_fp_linear_upwind_equals_central_plus_reformulated_dissipation(
             lam = np.maximum(lam, np.abs([U - a, U, U, U, U + a]))
         central = c6 @ Ft[st]
         diffQ = (Qt - Qs[None, :] * invJ[:, None])[st]      # Q~_m - Q~*_m
-        diss = R @ (lam * (L @ (d5 @ diffQ)))
+        if charwise:
+            diss = R @ (lam * (L @ (d5 @ diffQ)))
+        else:
+            diss = max(lam[0], lam[4]) * (d5 @ diffQ)
         ref = central + diss
         assert np.abs(got - ref).max() < 1e-12 * (1 + np.abs(ref).max())
 
