@@ -226,9 +226,13 @@ typedef struct fp_pipe fp_pipe;
    to autotune when autotune is nonzero).  Allocates the device states and the batches. */
 int fp_pipe_create(fp_ctx *const *blocks, int nblocks, const void *const *q_host, int ngroups,
                    int autotune, fp_pipe **out);
-/* One RK3 step of size dt: q_host[b] is copied in, advanced and copied back, in place.  The
-   work is ordered after earlier work on `stream`, and `stream` waits for all of it; the host
-   states are complete once `stream` is synchronised. */
+/* One RK3 step of size dt: q_host[b] is copied in, advanced and copied back, in place.  Each
+   group's work follows that group's work of the previous step (its own stream), so consecutive
+   steps overlap; `stream` waits for all of it, and the host states are complete once `stream`
+   is synchronised.  The pipe's work is not ordered after work the caller queued earlier on
+   `stream`, so the pipe's contexts (and their stage and residual scratch) must not be used by
+   other calls (fp_rhs, fp_rk3_step, a batch) while a pipe step may be in flight: synchronise
+   `stream` before such a call. */
 int fp_pipe_rk3_step_host(fp_pipe *pipe, void *const *q_host, double dt, void *stream);
 int fp_pipe_groups(const fp_pipe *pipe);
 int fp_pipe_launches_per_step(const fp_pipe *pipe);

@@ -124,7 +124,8 @@ class Batch:
 class Pipe:
     """Blocks whose states live in host memory (page-locked CPU tensors), advanced with
     the host<->device copies overlapped by compute (fp_pipe_*): the blocks are split into
-    `groups` batches with a stream each."""
+    `groups` batches with a stream each.  Steps run on the pipe's own streams, so the blocks
+    must not be used by other calls while a step may be in flight (synchronise first)."""
 
     def __init__(self, blocks, host_states, groups=4, autotune=True):
         self.blocks = list(blocks)

@@ -742,7 +742,9 @@ def test_pipe_host_states_equal_the_device_batch():
     ref = [q.clone() for q in states]
     hosts = [q.cpu().pin_memory() for q in states]
     from paper_2101_05886_gb300.solver import Pipe
-    pipe = Pipe(blocks, hosts, groups=3, autotune=True)
+    # the pipe's steps run on its own streams: the reference batch gets contexts of its own
+    pblocks = [Block(g, metric_order=6, precision=F32, q_inf=qinf) for g in grids]
+    pipe = Pipe(pblocks, hosts, groups=3, autotune=True)
     assert B.fp_pipe_groups(pipe.pipe) == 3
     bat = Batch(blocks, ref, autotune=False)
     for _ in range(3):
@@ -753,7 +755,7 @@ def test_pipe_host_states_equal_the_device_batch():
         assert torch.equal(h, r.cpu())
     pipe.close()
     bat.close()
-    for b in blocks:
+    for b in blocks + pblocks:
         b.close()
 
 
