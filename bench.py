@@ -231,9 +231,14 @@ def run_gpu(args):
         pipe.close()
         del hosts
 
-    # ---- roofline of the dominant kernel (the sweep; every launch in the graph is one)
+    # ---- roofline of the dominant kernel (the sweep; every launch in the graph is one).  A
+    # direction pass over all blocks is `launches_per_pass` concurrent launches (one per graph
+    # branch, each on its share of the blocks), so the unit is the pass: its algorithmic work
+    # over the pass time (graph time / passes)
     hbm, src = peaks()
-    per_launch_ms = graph_ms / (args.steps * launches_per_step)
+    passes_per_step = 3 * 3
+    launches_per_pass = launches_per_step // passes_per_step
+    per_launch_ms = graph_ms / (args.steps * passes_per_step)
     alg_bytes_per_launch = BYTES_PER_CELL_STAGE_F32 * ncells / 3.0     # one of the 3 direction passes
     achieved_gbs = alg_bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
     flops_per_launch = FLOPS_PER_POINT_PASS_F32 * ncells
@@ -242,8 +247,9 @@ def run_gpu(args):
             "unit": "TFLOP/s", "frac": round(achieved_tf / FP32_PEAK_TFLOPS, 4),
             "traffic": round(TRAFFIC_BYTES_PER_POINT_PASS * ncells) if args.blocks == 64 else None,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (maximum SM clock)",
-            "kernel": "fpk::fp_sweep<float,6,0>", "launch_ms": round(per_launch_ms, 4),
-            "algorithmic_flops_per_launch": flops_per_launch,
+            "kernel": "fpk::fp_sweep<float,6,0>", "pass_ms": round(per_launch_ms, 4),
+            "launches_per_pass": launches_per_pass,
+            "algorithmic_flops_per_pass": flops_per_launch,
             "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(achieved_gbs / hbm, 4), "peak_source": src,
                     "algorithmic_bytes_per_point_stage": round(BYTES_PER_CELL_STAGE_F32, 1)}}

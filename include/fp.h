@@ -187,7 +187,9 @@ void fp_free(fp_ctx *ctx);                 /* NULL-safe; synchronises the device
    A batch advances many independent blocks (same precision, scheme, metric order)
    together: one persistent launch per direction pass covers the work of every
    block, the three RK stages are captured once into a CUDA graph, and each call
-   replays it.  The batch keeps pointers to the contexts (they must outlive it)
+   replays it.  Unlinked batches with local Lax-Friedrichs speeds are captured as two
+   independent chains of the graph, each advancing half of the blocks (by points), so the
+   chains' launches run side by side on the GPU.  The batch keeps pointers to the contexts (they must outlive it)
    and to the caller's state buffers q_devs[b] given at creation.  When autotune
    is nonzero, fp_batch_create times each candidate tile shape on the blocks and
    keeps the fastest per size class; it may run kernels on the blocks' buffers. */

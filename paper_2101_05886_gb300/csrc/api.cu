@@ -59,6 +59,13 @@ struct fp_batch {
   cudaGraphExec_t exec = nullptr;
   int dims = 3, M = 6, scheme = 0, charwise = 1, fp = 1, is_f32 = 1, global_lf = 0;
   int bnd[3] = {0, 0, 0};   // some block has a slip-wall or cut side in direction d
+  // Graph branches: groups of blocks whose RK steps run as independent chains of the graph,
+  // so one group's launches fill the end-of-pass tail of another's.  One branch when blocks
+  // are linked (a block reads its neighbours' stage states) or the LF speeds are global.
+  static constexpr int kMaxBranch = 2;
+  int nbranch = 1;
+  int2 *bitems[kMaxBranch][3] = {};
+  int bnitems[kMaxBranch][3] = {};
   int per_sm = 1, nsm = 152;
   int2 *lam_items = nullptr;
   int nlam_items = 0;
@@ -537,6 +544,8 @@ void fp_batch_free(fp_batch *b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   cudaFree(b->dblk);
   for (int d = 0; d < 3; ++d) cudaFree(b->items[d]);
+  for (int g = 0; g < fp_batch::kMaxBranch; ++g)
+    for (int d = 0; d < 3; ++d) cudaFree(b->bitems[g][d]);
   cudaFree(b->dt_dev);
   if (b->dt_host) cudaFreeHost(b->dt_host);
   if (b->dt_ready) cudaEventDestroy(b->dt_ready);
@@ -546,9 +555,17 @@ void fp_batch_free(fp_batch *b) {
 
 const char *fp_batch_last_error(const fp_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
-int fp_batch_launches_per_step(const fp_batch *b) { return b ? 3 * (b->dims + (b->global_lf ? 2 : 0)) : 0; }
+int fp_batch_launches_per_step(const fp_batch *b) {
+  return b ? b->nbranch * 3 * (b->dims + (b->global_lf ? 2 : 0)) : 0;
+}
+
+static int batch_items_into(fp_batch *b, int d, const std::vector<int> *only_blocks, int2 **dst, int *ndst);
 
 static int batch_items(fp_batch *b, int d, const std::vector<int> *only_blocks) {
+  return batch_items_into(b, d, only_blocks, &b->items[d], &b->nitems[d]);
+}
+
+static int batch_items_into(fp_batch *b, int d, const std::vector<int> *only_blocks, int2 **dst, int *ndst) {
   std::vector<std::pair<long long, int2>> work;
   for (size_t k = 0; k < b->hblk.size(); ++k) {
     if (only_blocks && std::find(only_blocks->begin(), only_blocks->end(), (int)k) == only_blocks->end())
@@ -566,12 +583,12 @@ static int batch_items(fp_batch *b, int d, const std::vector<int> *only_blocks) 
                    });
   std::vector<int2> it(work.size());
   for (size_t k = 0; k < work.size(); ++k) it[k] = work[k].second;
-  cudaFree(b->items[d]);
-  b->items[d] = nullptr;
-  b->nitems[d] = (int)it.size();
+  cudaFree(*dst);
+  *dst = nullptr;
+  *ndst = (int)it.size();
   if (it.empty()) return FP_OK;
-  cudaError_t e = cudaMalloc(&b->items[d], it.size() * sizeof(int2));
-  if (e == cudaSuccess) e = cudaMemcpy(b->items[d], it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMalloc(dst, it.size() * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMemcpy(*dst, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch items: ") + cudaGetErrorString(e));
   return FP_OK;
 }
@@ -584,11 +601,12 @@ static int batch_upload(fp_batch *b, cudaStream_t s) {
   return FP_OK;
 }
 
-static int batch_pass(fp_batch *b, int d, int mode, int stage, cudaStream_t s) {
+static int batch_pass_items(fp_batch *b, int d, int mode, int stage, cudaStream_t s, const int2 *items,
+                            int nitems) {
   fpk::SweepLaunch L;
   L.blocks = b->dblk;
-  L.items = b->items[d];
-  L.nitems = b->nitems[d];
+  L.items = items;
+  L.nitems = nitems;
   L.dir = d;
   L.mode = mode;
   L.stage = stage;
@@ -598,6 +616,10 @@ static int batch_pass(fp_batch *b, int d, int mode, int stage, cudaStream_t s) {
   cudaError_t e = launch(b->is_f32, L, b->M, b->scheme, b->charwise, b->fp, s);
   if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
   return FP_OK;
+}
+
+static int batch_pass(fp_batch *b, int d, int mode, int stage, cudaStream_t s) {
+  return batch_pass_items(b, d, mode, stage, s, b->items[d], b->nitems[d]);
 }
 
 // Autotuner: for each direction and each line-length class, time every tile shape
@@ -720,12 +742,53 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
   if (!st) st = batch_upload(b, s);
   for (int d = 0; d < b->dims && !st; ++d) st = batch_items(b, d, nullptr);
   if (st) { std::fprintf(stderr, "fp_batch_create: %s\n", b->err.c_str()); fp_batch_free(b); return st; }
-  // capture the three RK stages x directions into one graph
+  // graph branches: blocks split into groups of about equal size (largest first into the
+  // lightest group), each group's items built separately
+  if (!b->global_lf && nlinks == 0 && nblocks >= fp_batch::kMaxBranch) {
+    b->nbranch = fp_batch::kMaxBranch;
+    std::vector<int> order(nblocks);
+    for (int k = 0; k < nblocks; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return blocks[x]->ncells > blocks[y]->ncells; });
+    std::vector<std::vector<int>> grp(b->nbranch);
+    std::vector<long long> load(b->nbranch, 0);
+    for (int k : order) {
+      const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      grp[g].push_back(k);
+      load[g] += blocks[k]->ncells;
+    }
+    for (int g = 0; g < b->nbranch && !st; ++g)
+      for (int d = 0; d < b->dims && !st; ++d) st = batch_items_into(b, d, &grp[g], &b->bitems[g][d], &b->bnitems[g][d]);
+    if (st) { fp_batch_free(b); return st; }
+  }
+  // capture the three RK stages x directions into one graph (one chain per branch)
   cudaStream_t cs;
   e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) { fp_batch_free(b); return FP_ERR_CUDA; }
-  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
+  cudaStream_t bs[fp_batch::kMaxBranch] = {};
+  cudaEvent_t fork = nullptr, join[fp_batch::kMaxBranch] = {};
+  if (b->nbranch > 1) {
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int g = 0; g < b->nbranch && e == cudaSuccess; ++g) {
+      e = cudaStreamCreateWithFlags(&bs[g], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[g], cudaEventDisableTiming);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess && b->nbranch > 1) {
+    e = cudaEventRecord(fork, cs);
+    for (int g = 0; g < b->nbranch && e == cudaSuccess && !st; ++g) {
+      e = cudaStreamWaitEvent(bs[g], fork, 0);
+      for (int stage = 0; stage < 3 && !st && e == cudaSuccess; ++stage)
+        for (int d = 0; d < b->dims && !st; ++d) {
+          int mode = d == 0 ? fpk::MODE_WRITE : (d == b->dims - 1 ? fpk::MODE_RK : fpk::MODE_ADD);
+          st = batch_pass_items(b, d, mode, stage, bs[g], b->bitems[g][d], b->bnitems[g][d]);
+        }
+      if (e == cudaSuccess) e = cudaEventRecord(join[g], bs[g]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, join[g], 0);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
+    if (e == cudaSuccess) e = e2;
+  } else if (e == cudaSuccess) {
     for (int stage = 0; stage < 3 && !st; ++stage) {
       if (b->global_lf) {
         cudaError_t el = fpk::launch_lambda(b->dblk, (int)b->hblk.size(), b->lam_items, b->nlam_items,
@@ -742,6 +805,11 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
   }
   if (e == cudaSuccess && !st) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   cudaStreamDestroy(cs);
+  for (int g = 0; g < fp_batch::kMaxBranch; ++g) {
+    if (bs[g]) cudaStreamDestroy(bs[g]);
+    if (join[g]) cudaEventDestroy(join[g]);
+  }
+  if (fork) cudaEventDestroy(fork);
   if (e != cudaSuccess || st) {
     std::fprintf(stderr, "fp_batch_create: graph: %s %s\n", cudaGetErrorString(e), b->err.c_str());
     fp_batch_free(b);
