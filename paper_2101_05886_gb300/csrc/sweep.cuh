@@ -715,6 +715,24 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           c[4] = X4 - Y4;
         };
 
+        // the same projection of two stencil points at once (the rows are the face's)
+        auto project_pair = [&](const P d[5], P c[5]) {
+          if (!charwise) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) c[v] = pmul(pc<P>(T(0.5)), d[v]);
+            return;
+          }
+          const P ud = pfma(pc<P>(u[0]), d[1], pfma(pc<P>(u[1]), d[2], pmul(pc<P>(u[2]), d[3])));
+          const P X4 = pmul(pc<P>(qbb), pfma(pc<P>(hq2), d[0], psub(d[4], ud)));
+          const P nd = pfma(pc<P>(n[0]), d[1], pfma(pc<P>(n[1]), d[2], pmul(pc<P>(n[2]), d[3])));
+          const P Y4 = pmul(pc<P>(qcs), psub(pmul(pc<P>(Un), d[0]), nd));
+          c[0] = padd(X4, Y4);
+          c[1] = pfma(pc<P>(T(-2)), X4, pmul(pc<P>(T(0.5)), d[0]));
+          c[2] = pfma(pc<P>(h1[0]), d[1], pfma(pc<P>(h1[1]), d[2], pfma(pc<P>(h1[2]), d[3], pmul(pc<P>(-hut1), d[0]))));
+          c[3] = pfma(pc<P>(h2[0]), d[1], pfma(pc<P>(h2[1]), d[2], pfma(pc<P>(h2[2]), d[3], pmul(pc<P>(-hut2), d[0]))));
+          c[4] = psub(X4, Y4);
+        };
+
         // split stencil values f+/- for the NS stencil points
         T fpl[NS][5], fmi[NS][5];
         // f+- = (1/2) l.(dF +- lambda d (1/J)_m) of one stencil point
@@ -745,12 +763,19 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
               uBp[c] = pmk(CELL(CF_U + c, q), CELL(CF_U + c, q2));
             }
             dflux_pair<T>(g1, pmk(CELL(CF_RINV, q), CELL(CF_RINV, q2)), uBp, us, ms, Qs[4], ps, dp, kp2, out);
-            const T dF0[5] = {out[0].x, out[1].x, out[2].x, out[3].x, out[4].x};
-            const T d0[5] = {dp[0].x, dp[1].x, dp[2].x, dp[3].x, dp[4].x};
-            split_point(s, dF0, d0, CELL(CF_INVJ, q));
-            const T dF1[5] = {out[0].y, out[1].y, out[2].y, out[3].y, out[4].y};
-            const T d1[5] = {dp[0].y, dp[1].y, dp[2].y, dp[3].y, dp[4].y};
-            split_point(s + 1, dF1, d1, CELL(CF_INVJ, q2));
+            P cF[5], cD[5];
+            project_pair(out, cF);
+            project_pair(dp, cD);
+            const T ij0 = CELL(CF_INVJ, q), ij1 = CELL(CF_INVJ, q2);
+            const T mu0[5] = {lam[0] * ij0, lam[1] * ij0, lam[1] * ij0, lam[1] * ij0, lam[4] * ij0};
+            const T mu1[5] = {lam[0] * ij1, lam[1] * ij1, lam[1] * ij1, lam[1] * ij1, lam[4] * ij1};
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+              fpl[s][v] = cF[v].x + mu0[v] * cD[v].x;
+              fmi[s][v] = cF[v].x - mu0[v] * cD[v].x;
+              fpl[s + 1][v] = cF[v].y + mu1[v] * cD[v].y;
+              fmi[s + 1][v] = cF[v].y - mu1[v] * cD[v].y;
+            }
           }
         } else {
           // plain scheme: F~_m and Q~_m themselves
