@@ -749,10 +749,14 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           }
         };
         if (fpform) {
-          // reference-state differences of the stencil points two at a time (packed)
+          // reference-state differences of the stencil points two at a time (packed): points
+          // s and its mirror NS-1-s, whose f+ and f- are the (+, -) lanes of the reconstruction
+          // pair s; the mirror pair NS-1-s is formed lane by lane
+          const P lpm[3] = {pmk(lam[0], -lam[0]), pmk(lam[1], -lam[1]), pmk(lam[4], -lam[4])};
 #pragma unroll
-          for (int s = 0; s < NS; s += 2) {
-            const int q = s + Q0, q2 = s + Q0 + 1;
+          for (int s = 0; s < NS / 2; ++s) {
+            const int mir = NS - 1 - s;
+            const int q = s + Q0, q2 = mir + Q0;
             P dp[5], kp2[3], uBp[3], out[5];
 #pragma unroll
             for (int v = 0; v < 5; ++v)
@@ -766,15 +770,17 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
             P cF[5], cD[5];
             project_pair(out, cF);
             project_pair(dp, cD);
-            const T ij0 = CELL(CF_INVJ, q), ij1 = CELL(CF_INVJ, q2);
-            const T mu0[5] = {lam[0] * ij0, lam[1] * ij0, lam[1] * ij0, lam[1] * ij0, lam[4] * ij0};
-            const T mu1[5] = {lam[0] * ij1, lam[1] * ij1, lam[1] * ij1, lam[1] * ij1, lam[4] * ij1};
+            // (lambda (1/J)_s, -lambda (1/J)_mirror) for the three speed classes
+            const P ijp = pmk(CELL(CF_INVJ, q), CELL(CF_INVJ, q2));
+            const P mp[3] = {pmul(lpm[0], ijp), pmul(lpm[1], ijp), pmul(lpm[2], ijp)};
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-              fpl[s][v] = cF[v].x + mu0[v] * cD[v].x;
-              fmi[s][v] = cF[v].x - mu0[v] * cD[v].x;
-              fpl[s + 1][v] = cF[v].y + mu1[v] * cD[v].y;
-              fmi[s + 1][v] = cF[v].y - mu1[v] * cD[v].y;
+              const P &mv = mp[v == 0 ? 0 : (v == 4 ? 2 : 1)];
+              const P r = pfma(mv, cD[v], cF[v]);                 // (f+ of s, f- of the mirror)
+              fpl[s][v] = r.x;
+              fmi[mir][v] = r.y;
+              fmi[s][v] = cF[v].x - mv.x * cD[v].x;
+              fpl[mir][v] = cF[v].y - mv.y * cD[v].y;
             }
           }
         } else {
