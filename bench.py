@@ -43,9 +43,11 @@ BYTES_PER_CELL_STAGE_F64 = 2 * BYTES_PER_CELL_STAGE_F32
 FLOPS_PER_POINT_PASS_F32 = 2280.0
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes per launch measured by ncu for the current kernel (16-block capture, mean of the
-# three passes 95.4 B per point per pass), scaled to a launch over the 64-block workload.
-TRAFFIC_BYTES_PER_POINT_PASS = 95.4
+# DRAM bytes per point per direction pass measured by ncu for the current kernel (16-block
+# capture of two RK stages of one graph branch; mean over an RK step, whose second and third
+# stages also read Q^n in the last pass: 95.7-97.0 B depending on the branch captured), scaled
+# to a pass over the 64-block workload.
+TRAFFIC_BYTES_PER_POINT_PASS = 96.4
 
 
 def _dist():
