@@ -252,6 +252,34 @@ def test_batch_matches_single_blocks_bitwise(precision):
         b.close()
 
 
+def test_batch_graph_branches_and_launch_counts():
+    """An unlinked batch of two or more blocks with local LF speeds runs its RK step as two
+    graph branches (two launches per direction pass); one block, or global LF speeds (two
+    reduction launches per stage), keep one chain.  The global-LF batch step equals per-block
+    steps bit for bit."""
+    grids, qinf, blocks, states = _mini_batch(F32)
+    two = Batch(blocks, states, autotune=False)
+    assert two.launches_per_step() == 2 * 3 * 3
+    two.close()
+    one = Batch(blocks[:1], states[:1], autotune=False)
+    assert one.launches_per_step() == 3 * 3
+    one.close()
+    gblocks = [Block(g, metric_order=6, precision=F32, q_inf=qinf, global_lf=1) for g in grids]
+    glf = Batch(gblocks, states, autotune=False)
+    assert glf.launches_per_step() == 3 * (3 + 2)
+    copies = [q.clone() for q in states]
+    dt = 1e-3
+    glf.rk3_step(dt)
+    for blk, q in zip(gblocks, copies):
+        blk.rk3_step(q, dt)
+    torch.cuda.synchronize()
+    for a, b in zip(states, copies):
+        assert torch.equal(a, b)
+    glf.close()
+    for b in blocks + gblocks:
+        b.close()
+
+
 def test_batch_rk3_parity_with_oracle_fp64():
     grids, qinf, blocks, states = _mini_batch(F64, M=4)
     q0 = [s.cpu().numpy() for s in states]
