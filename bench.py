@@ -4,7 +4,8 @@ Default workload: 64 blocks of seeded uneven sizes (each side U{32..128}; half
 cylinder O-grids, half periodic wavy grids), Mach 3 stream with a 1e-3 smooth
 perturbation, WENO5-JS FP form, 6th-order metrics, FP32 state and arithmetic on
 FP64-built metrics, all blocks advanced by one CUDA-graph replay per SSP-RK3
-step (one persistent launch per direction pass), autotuned tiles.
+step (two independent chains of the graph, each with half of the blocks and one
+persistent launch per direction pass), autotuned tiles.
 
 Metric: Mcell-RHS/s per RK stage = interior points x RK stages / second.
 Prints one JSON line (rank 0).  --impl reference times the serial FP64 oracle

@@ -189,7 +189,8 @@ void fp_free(fp_ctx *ctx);                 /* NULL-safe; synchronises the device
    block, the three RK stages are captured once into a CUDA graph, and each call
    replays it.  Unlinked batches with local Lax-Friedrichs speeds are captured as two
    independent chains of the graph, each advancing half of the blocks (by points), so the
-   chains' launches run side by side on the GPU.  The batch keeps pointers to the contexts (they must outlive it)
+   chains' launches run side by side on the GPU (then one launch per chain covers that
+   chain's blocks).  The batch keeps pointers to the contexts (they must outlive it)
    and to the caller's state buffers q_devs[b] given at creation.  When autotune
    is nonzero, fp_batch_create times each candidate tile shape on the blocks and
    keeps the fastest per size class; it may run kernels on the blocks' buffers. */
