@@ -242,6 +242,15 @@ int fp_pipe_launches_per_step(const fp_pipe *pipe);
 const char *fp_pipe_last_error(const fp_pipe *pipe);
 void fp_pipe_free(fp_pipe *pipe);          /* NULL-safe; synchronises the pipe's streams */
 
+/* ---------------- host helper (no counterpart in the paper) ----------------
+   The partition behind the graph branches of fp_batch_create (weights = points per block)
+   and the groups of fp_pipe_create (weights = state bytes per block).  Items go one at a
+   time, heaviest first (equal weights in index order), each into the currently lightest of
+   `ngroups` groups (the lowest index among equally light ones); group_of[k] receives the
+   group of item k.  Host only: no CUDA call, no allocation visible to the caller.
+   FP_ERR_ARG for a null pointer with n > 0, n < 0, ngroups < 1 or a negative weight. */
+int fp_balanced_groups(const long long *weights, int n, int ngroups, int *group_of);
+
 #ifdef __cplusplus
 }
 #endif

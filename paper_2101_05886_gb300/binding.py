@@ -26,6 +26,7 @@ EXPORTS = [
     "fp_free", "fp_batch_create", "fp_batch_create_linked", "fp_batch_rk3_step", "fp_batch_rhs", "fp_batch_launches_per_step",
     "fp_batch_last_error", "fp_batch_free", "fp_state_bytes", "fp_pipe_create", "fp_pipe_rk3_step_host",
     "fp_pipe_groups", "fp_pipe_launches_per_step", "fp_pipe_last_error", "fp_pipe_free",
+    "fp_balanced_groups",
 ]
 
 
@@ -95,6 +96,8 @@ def lib():
         L.fp_pipe_last_error.restype = ctypes.c_char_p
         L.fp_pipe_free.argtypes = [_VP]
         L.fp_pipe_free.restype = None
+        L.fp_balanced_groups.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]
         _lib = L
     return _lib
 
@@ -281,3 +284,14 @@ def fp_pipe_launches_per_step(pipe):
 
 def fp_pipe_free(pipe):
     lib().fp_pipe_free(pipe)
+
+
+def fp_balanced_groups(weights, ngroups):
+    """Group index of each weighted item (the partition of batch branches and pipe groups)."""
+    n = len(weights)
+    w = (ctypes.c_longlong * max(n, 1))(*[int(x) for x in weights])
+    out = (ctypes.c_int * max(n, 1))()
+    st = lib().fp_balanced_groups(w, n, int(ngroups), out)
+    if st != FP_OK:
+        raise FPError(st, "fp_balanced_groups: invalid arguments")
+    return list(out[:n])

@@ -742,20 +742,16 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
   if (!st) st = batch_upload(b, s);
   for (int d = 0; d < b->dims && !st; ++d) st = batch_items(b, d, nullptr);
   if (st) { std::fprintf(stderr, "fp_batch_create: %s\n", b->err.c_str()); fp_batch_free(b); return st; }
-  // graph branches: blocks split into groups of about equal size (largest first into the
-  // lightest group), each group's items built separately
+  // graph branches: blocks split into groups of about equal point count, each group's
+  // items built separately
   if (!b->global_lf && nlinks == 0 && nblocks >= fp_batch::kMaxBranch) {
     b->nbranch = fp_batch::kMaxBranch;
-    std::vector<int> order(nblocks);
-    for (int k = 0; k < nblocks; ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return blocks[x]->ncells > blocks[y]->ncells; });
+    std::vector<long long> weight(nblocks);
+    for (int k = 0; k < nblocks; ++k) weight[k] = blocks[k]->ncells;
+    std::vector<int> group_of(nblocks);
+    fp_balanced_groups(weight.data(), nblocks, b->nbranch, group_of.data());
     std::vector<std::vector<int>> grp(b->nbranch);
-    std::vector<long long> load(b->nbranch, 0);
-    for (int k : order) {
-      const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-      grp[g].push_back(k);
-      load[g] += blocks[k]->ncells;
-    }
+    for (int k = 0; k < nblocks; ++k) grp[group_of[k]].push_back(k);
     for (int g = 0; g < b->nbranch && !st; ++g)
       for (int d = 0; d < b->dims && !st; ++d) st = batch_items_into(b, d, &grp[g], &b->bitems[g][d], &b->bnitems[g][d]);
     if (st) { fp_batch_free(b); return st; }

@@ -1,5 +1,6 @@
 // pipe.cu - batched advance of host-resident states with the host<->device copies
-// overlapped by compute (C ABI in include/fp.h: fp_pipe_*).
+// overlapped by compute (C ABI in include/fp.h: fp_pipe_*), and the balanced partition that the
+// pipe's groups and the batch graph's branches use (fp_balanced_groups).
 //
 // The blocks are split into groups of about equal size.  Each group is a batch
 // (fp_batch_create: one persistent launch per direction pass, the three RK stages in
@@ -60,22 +61,17 @@ int fp_pipe_create(fp_ctx *const *blocks, int nblocks, const void *const *q_host
     if (!blocks[k] || !q_host[k] || fp_state_bytes(blocks[k]) == 0) return FP_ERR_ARG;
   ngroups = std::min(ngroups, nblocks);
   fp_pipe *p = new fp_pipe();
+  std::vector<long long> weight(nblocks);
   for (int k = 0; k < nblocks; ++k) {
     p->ctx.push_back(blocks[k]);
     p->bytes.push_back(fp_state_bytes(blocks[k]));
+    weight[k] = (long long)p->bytes[k];
   }
-  // groups of about equal size: largest block first into the lightest group
-  std::vector<int> order(nblocks);
-  for (int k = 0; k < nblocks; ++k) order[k] = k;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p->bytes[a] > p->bytes[b]; });
+  // groups of about equal size (block indices ascending within a group)
+  std::vector<int> group_of(nblocks);
+  fp_balanced_groups(weight.data(), nblocks, ngroups, group_of.data());
   p->groups.assign(ngroups, {});
-  std::vector<size_t> load(ngroups, 0);
-  for (int k : order) {
-    const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-    p->groups[g].push_back(k);
-    load[g] += p->bytes[k];
-  }
-  for (auto &g : p->groups) std::sort(g.begin(), g.end());
+  for (int k = 0; k < nblocks; ++k) p->groups[group_of[k]].push_back(k);
   // device states, initialised from the host states (so autotuning runs on real data)
   p->qdev.assign(nblocks, nullptr);
   for (int k = 0; k < nblocks; ++k) {
@@ -154,5 +150,21 @@ int fp_pipe_launches_per_step(const fp_pipe *p) {
 }
 
 const char *fp_pipe_last_error(const fp_pipe *p) { return p ? p->err.c_str() : "null pipe"; }
+
+int fp_balanced_groups(const long long *weights, int n, int ngroups, int *group_of) {
+  if (n < 0 || ngroups < 1 || (n > 0 && (!weights || !group_of))) return FP_ERR_ARG;
+  for (int k = 0; k < n; ++k)
+    if (weights[k] < 0) return FP_ERR_ARG;
+  std::vector<int> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return weights[a] > weights[b]; });
+  std::vector<long long> load(ngroups, 0);
+  for (int k : order) {
+    const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    group_of[k] = g;
+    load[g] += weights[k];
+  }
+  return FP_OK;
+}
 
 }  // extern "C"

@@ -96,3 +96,51 @@ def test_pipe_and_link_calls_reject_null_arguments(lib):
     links = (B.fp_block_link * 1)(B.fp_block_link(0, 0, 1, 0))
     assert lib.fp_batch_create_linked(None, 1, None, links, 1, 0, None, ctypes.byref(out)) == B.FP_ERR_ARG
     assert lib.fp_batch_create_linked(None, 1, None, None, 1, 0, None, ctypes.byref(out)) == B.FP_ERR_ARG
+
+
+def test_balanced_groups_rule(lib):
+    """Heaviest first, each into the lightest group; ties in index order and to the lower group."""
+    assert B.fp_balanced_groups([5, 5, 5, 5], 2) == [0, 1, 0, 1]
+    assert B.fp_balanced_groups([1, 9, 3], 2) == [1, 0, 1]
+    assert B.fp_balanced_groups([7, 2, 2, 3], 3) == [0, 2, 2, 1]   # 7, 3, then both 2s into the third
+    assert B.fp_balanced_groups([4, 1], 5) == [0, 1]
+    assert B.fp_balanced_groups([], 2) == []
+
+
+def test_balanced_groups_lpt_bound_by_brute_force(lib):
+    """Graham's bound for longest-processing-time-first scheduling on m groups: the heaviest
+    group is at most (4/3 - 1/(3m)) of the optimum, found here by enumerating every partition;
+    and no group is heavier than the lightest by more than the heaviest item."""
+    import itertools
+    rng = np.random.default_rng(11)
+    for trial in range(60):
+        m = 2 + trial % 2
+        n = int(rng.integers(1, 9))
+        w = [int(x) for x in rng.integers(1, 1000, size=n)]
+        g = B.fp_balanced_groups(w, m)
+        load = [sum(wk for wk, gk in zip(w, g) if gk == j) for j in range(m)]
+        best = min(max(sum(wk for wk, gk in zip(w, a) if gk == j) for j in range(m))
+                   for a in itertools.product(range(m), repeat=n))
+        assert max(load) * 3 * m <= best * (4 * m - 1)
+        assert max(load) - min(load) <= max(w)
+
+
+def test_balanced_groups_on_the_batched_workload_subset(lib):
+    """The 16-block subset of the batched workload splits 5,608,608 / 5,683,224 points."""
+    from paper_2101_05886_gb300 import inputs as I
+    sizes = I.batched_block_sizes(64, 32, 128, 4)[:16]
+    w = [int(np.prod(n)) for n in sizes]
+    g = B.fp_balanced_groups(w, 2)
+    assert [sum(wk for wk, gk in zip(w, g) if gk == j) for j in range(2)] == [5608608, 5683224]
+
+
+def test_balanced_groups_rejects_invalid_arguments(lib):
+    one = (ctypes.c_longlong * 1)(1)
+    out = (ctypes.c_int * 1)()
+    assert lib.fp_balanced_groups(None, 1, 2, out) == B.FP_ERR_ARG
+    assert lib.fp_balanced_groups(one, 1, 2, None) == B.FP_ERR_ARG
+    assert lib.fp_balanced_groups(one, -1, 2, out) == B.FP_ERR_ARG
+    assert lib.fp_balanced_groups(one, 1, 0, out) == B.FP_ERR_ARG
+    neg = (ctypes.c_longlong * 1)(-1)
+    assert lib.fp_balanced_groups(neg, 1, 2, out) == B.FP_ERR_ARG
+    assert lib.fp_balanced_groups(None, 0, 2, None) == B.FP_OK
