@@ -794,9 +794,10 @@ def _full_scale(dq):
 
 
 def test_full_size_batched_workload_sampled_parity():
-    """The 64-block batched workload at full size (34.5M points), in the launch configuration
-    the benchmark times (autotuned tiles, one persistent launch per pass over all blocks):
-    dQ/dt of sampled blocks against the oracle on interior sub-boxes.  FP32 on a Mach 3
+    """The 64-block batched workload at full size (34.5M points) with the benchmark's autotuned
+    tiles and persistent launches (the residual call runs one launch per pass over all blocks;
+    the timed graph runs the same kernel over two halves of the blocks, equal per block bit for
+    bit, see the batch tests): dQ/dt of sampled blocks against the oracle on interior sub-boxes.  FP32 on a Mach 3
     stream with a 1e-3 perturbation: bound 3e-5 of each block's residual scale."""
     M = 6
     Gn = O.node_ghost(M)
