@@ -45,7 +45,9 @@ typedef enum {
   FP_ERR_CUDA = 2,         /* CUDA runtime error (possibly from earlier async work) */
   FP_ERR_OOM = 3,          /* device allocation failed */
   FP_ERR_NONFINITE = 4,    /* a kernel produced a non-finite state value */
-  FP_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  FP_ERR_TIMEOUT = 5,      /* reserved: a bounded device-side wait gave up.  No kernel of this
+                              library waits on another (work items are assigned statically and
+                              no launch waits on a flag), so no call returns it at present */
   FP_ERR_UNSUPPORTED = 6   /* valid but not implemented combination */
 } fp_status;
 
@@ -86,7 +88,9 @@ typedef struct {
                                    indices, read at the same RK stage; single-block calls
                                    (fp_rhs, fp_rk3_step, fp_rhs_noalloc) reject such blocks */
   double gamma;               /* ratio of specific heats (Sec. 2.1 Eq. EOS: 1.4) */
-  double q_inf[5];            /* far-field state; also the reference state of the FP32 form */
+  double q_inf[5];            /* far-field state; also the reference state of the FP32 form.
+                                 With FP_F32_MIXED it is used as float values, like the state
+                                 (a far-field ghost is a float state value) */
   int global_lf;              /* 0 = local Lax-Friedrichs speeds (max over the face's stencil),
                                  1 = global speeds (max over the block, per direction and
                                  characteristic field, refreshed every RK stage); Sec. 4 uses
@@ -140,25 +144,43 @@ int fp_get_metrics(fp_ctx *ctx, double *host_out);
    ordered like the state with n_dir+1 faces along dir (face f+1/2, f = -1..n-1). */
 int fp_get_face_metrics(fp_ctx *ctx, int dir, double *host_out);
 
-/* Synchronise `stream`, read and clear the device status word (non-finite state,
-   bounded-wait timeout).  Returns FP_OK, FP_ERR_NONFINITE or FP_ERR_TIMEOUT. */
+/* Synchronise `stream`, read and clear the device status word.  Returns FP_OK, or
+   FP_ERR_NONFINITE when an RK stage produced a non-finite state value since the last read. */
 int fp_get_device_status(fp_ctx *ctx, void *stream);
 
-/* Allocation-free residual: the result of fp_rhs, for callers that cannot allocate
-   device memory where they step (a frozen memory pool, a fixed device-memory budget, a
-   loop that must not stall on an allocation).  The paper has no counterpart; this is
-   an interface of this library.  The residual accumulator the direction passes share
-   is a file-scope static device array of 8 MiB (every GPU that loads the library holds
-   it until the process exits), and the block descriptor is a static device variable:
-   the call allocates nothing and frees nothing.  Blocks needing more than 8 MiB of
-   accumulator (more than 209,715 points in FP64, 419,430 in FP32) are rejected with
-   FP_ERR_ARG and a message in fp_last_error().  The first call on a device looks up
-   the static arrays' device addresses; make that first call before any stream
-   capture.  All calls share the static arrays, which keep the last call's contents
-   (the accumulator is fully rewritten by every call, so nothing needs clearing):
-   calls that may overlap on the GPU (different streams, several host threads) race
-   and must be serialised by the caller.  q_dev, dqdt_dev and the context as in fp_rhs. */
+/* Allocation-free residual (no counterpart in the paper; an interface of this library).
+   Computes what fp_rhs computes, bit for bit, without allocating or freeing anything, for
+   callers that cannot allocate device memory at the point where they evaluate a residual:
+   a host framework that hands out device memory only from a pool it reserved up front, a
+   solver loop that runs under a fixed device-memory budget, or a real-time loop that must
+   not stall in the allocator.
+   The residual accumulator that the three direction passes share is a file-scope static
+   device array of 8 MiB, and the block descriptor its kernels read a static device variable;
+   the descriptor travels as a kernel argument.  Both arrays come into existence on a device
+   with the first fp_init_grid there (which also looks up their device addresses) and stay
+   until the process exits.  Blocks that need more than 8 MiB of accumulator (more than
+   209,715 points in FP64, 419,430 in FP32) are rejected with FP_ERR_ARG and a message in
+   fp_last_error().  The context's device must be current.  Every call on a device shares
+   the static arrays, which keep the last call's contents (each call rewrites the whole
+   accumulator before reading it, so nothing needs clearing): calls that may overlap on the
+   GPU (different streams, several host threads) race with each other and must be
+   serialised by the caller.  q_dev, dqdt_dev and the context as in fp_rhs. */
 int fp_rhs_noalloc(fp_ctx *ctx, const void *q_dev, void *dqdt_dev, void *stream);
+
+/* Measured arithmetic peaks of the current device (no counterpart in the paper; the
+   denominators of the sweep's roofline).  Times, with CUDA events on `stream` (best of
+   three after a warm-up), kernels in which every thread runs independent fused
+   multiply-add chains on all SMs: scalar FP32 FFMA, packed FP32x2 FFMA2 and FP64 DFMA.
+   Writes TFLOP/s (an FMA counts two flops, an FFMA2 four) to the three outputs.  Allocates
+   and frees a few MB of device memory; synchronises `stream`.  FP_ERR_ARG for a null output. */
+int fp_probe_peaks(double *fp32_tflops, double *fp32x2_tflops, double *fp64_tflops, void *stream);
+
+/* Host-side failure injection: the n-th device or page-locked allocation made by the
+   library from now on (n = 0: the next one) fails as if memory were exhausted, so that the
+   FP_ERR_OOM paths of fp_init_grid, fp_batch_create and fp_pipe_create (which release
+   everything allocated so far and return nothing) can be exercised without exhausting a
+   device.  n < 0 cancels a pending failure.  Process-wide; returns FP_OK. */
+int fp_debug_fail_allocation(int n);
 
 /* Bytes of one state array of the block: 5 x n_i x n_j x n_k elements of the precision's
    type (double for FP_F64, float for FP_F32_MIXED); 0 for a NULL context. */

@@ -62,6 +62,7 @@ def lib():
         L.or_wenocu6_parts.argtypes = [_D, _D, _D, _D]
         L.or_interp_coef.argtypes = [ctypes.c_int, _D]
         L.or_weno5.argtypes = [_D]
+        L.or_weno5_parts.argtypes = [_D, _D, _D]
         L.or_weno5.restype = ctypes.c_double
         L.or_lu5.argtypes = [_D]
         L.or_lu5.restype = ctypes.c_double
@@ -166,6 +167,14 @@ def weno5(v) -> float:
 def weno7(v) -> float:
     v = np.ascontiguousarray(v, dtype=np.float64)
     return lib().or_weno7(_p(v))
+
+
+def weno5_parts(v):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    q = np.zeros(3)
+    b = np.zeros(3)
+    lib().or_weno5_parts(_p(v), _p(q), _p(b))
+    return q, b
 
 
 def weno7_parts(v):

@@ -285,6 +285,9 @@ static void weno5_parts(const double v[5], double q[3], double beta[3]) {
 
 static const double C_OPT[3] = {0.1, 0.6, 0.3};
 
+/* the sub-stencil face values and smoothness indicators, exposed for the pins */
+void or_weno5_parts(const double v[5], double q[3], double beta[3]) { weno5_parts(v, q, beta); }
+
 double or_weno5(const double v[5]) {
   const double eps = 1.0e-6;
   double q[3], beta[3], alpha[3], s = 0.0;

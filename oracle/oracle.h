@@ -61,6 +61,7 @@ int or_ghost_s(int M, int scheme);   /* G = max(3 or 4 (WENO7), M/2) */
 int or_node_ghost_s(int M, int scheme);
 void or_interp_coef(int M, double c[8]);      /* face interpolation weights (Sec. 3) */
 double or_weno5(const double v[5]);           /* WENO5-JS of v[0..4] = f_{i-2..i+2} at i+1/2 */
+void or_weno5_parts(const double v[5], double q[3], double beta[3]);  /* its q_k and beta_k */
 double or_lu5(const double v[5]);             /* linear upwind 5 = WENO with optimal weights */
 double or_weno7(const double v[7]);           /* WENO7-JS of v[0..6] = f_{i-3..i+3} at i+1/2 */
 void or_weno7_parts(const double v[7], double q[4], double beta[4]);

@@ -26,7 +26,7 @@ EXPORTS = [
     "fp_free", "fp_batch_create", "fp_batch_create_linked", "fp_batch_rk3_step", "fp_batch_rhs", "fp_batch_launches_per_step",
     "fp_batch_last_error", "fp_batch_free", "fp_state_bytes", "fp_pipe_create", "fp_pipe_rk3_step_host",
     "fp_pipe_groups", "fp_pipe_launches_per_step", "fp_pipe_last_error", "fp_pipe_free",
-    "fp_balanced_groups",
+    "fp_balanced_groups", "fp_debug_fail_allocation", "fp_probe_peaks",
 ]
 
 
@@ -98,6 +98,8 @@ def lib():
         L.fp_pipe_free.restype = None
         L.fp_balanced_groups.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]
+        L.fp_debug_fail_allocation.argtypes = [ctypes.c_int]
+        L.fp_probe_peaks.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3 + [_VP]
         _lib = L
     return _lib
 
@@ -295,3 +297,17 @@ def fp_balanced_groups(weights, ngroups):
     if st != FP_OK:
         raise FPError(st, "fp_balanced_groups: invalid arguments")
     return list(out[:n])
+
+
+def fp_debug_fail_allocation(n):
+    """Make the n-th library allocation from now fail as out of memory (n < 0: cancel)."""
+    return lib().fp_debug_fail_allocation(int(n))
+
+
+def fp_probe_peaks(stream=0):
+    """Measured FP32 (FFMA), FP32x2 (FFMA2) and FP64 (DFMA) TFLOP/s of the current device."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = lib().fp_probe_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), stream)
+    if st != FP_OK:
+        raise FPError(st, "fp_probe_peaks")
+    return a.value, b.value, c.value

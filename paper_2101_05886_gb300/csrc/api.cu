@@ -4,9 +4,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -42,6 +44,7 @@ struct fp_ctx {
   int nitems[3] = {0, 0, 0};
   int per_sm = 1;
   int nsm = 152;
+  int dev = 0;                        // the device the context's memory lives on
   double dt_host = 0.0;
   std::string err;
 };
@@ -71,6 +74,81 @@ struct fp_batch {
   int nlam_items = 0;
   std::string err;
 };
+
+// ----------------------------------------------------------------- allocations
+//
+// Every device and page-locked allocation of the library goes through dev_malloc and
+// host_malloc.  fp_debug_fail_allocation arms a countdown on the host: the allocation that
+// finds it at zero returns cudaErrorMemoryAllocation without calling CUDA, so the failure
+// paths (FP_ERR_OOM, with everything allocated so far released) can be exercised without
+// exhausting a device.
+namespace {
+std::atomic<long long> g_fail_countdown{-1};   // -1: no failure armed
+
+bool take_scheduled_failure() {
+  long long cur = g_fail_countdown.load();
+  while (cur >= 0 && !g_fail_countdown.compare_exchange_weak(cur, cur - 1)) {
+  }
+  return cur == 0;
+}
+}  // namespace
+
+namespace fpk {
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  *p = nullptr;
+  if (take_scheduled_failure()) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+cudaError_t host_malloc(void **p, size_t bytes) {
+  *p = nullptr;
+  if (take_scheduled_failure()) return cudaErrorMemoryAllocation;
+  return cudaMallocHost(p, bytes);
+}
+}  // namespace fpk
+
+// ----------------------------------------------------------------- static scratch of fp_rhs_noalloc
+//
+// The residual accumulator that fp_rhs_noalloc's three direction passes share, and the block
+// descriptor its kernels read, live in file-scope device arrays rather than in memory the
+// call would have to allocate.  Host code cannot use the arrays' names as device addresses
+// (on the host they name a stand-in), so their addresses are looked up once per device with
+// that device current, in fp_init_grid: a call that allocates anyway, and the first use of
+// this file's module on the device, which is when the arrays come into existence there.
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;      // 8 MiB per device
+constexpr int kNoAllocMaxDevices = 64;
+__device__ __align__(256) unsigned char g_noalloc_racc[kNoAllocScratchBytes];
+__device__ __align__(256) BlockDev g_noalloc_block;
+
+struct NoAllocDevice {
+  void *racc = nullptr;
+  BlockDev *blk = nullptr;
+  std::atomic<bool> ready{false};
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// once per device, with that device current; safe from several host threads
+cudaError_t noalloc_prepare(int dev) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaSuccess;   // fp_rhs_noalloc refuses such devices
+  NoAllocDevice &S = g_noalloc_dev[dev];
+  if (S.ready.load(std::memory_order_acquire)) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (S.ready.load(std::memory_order_relaxed)) return cudaSuccess;
+  void *racc = nullptr, *blk = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&racc, g_noalloc_racc);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(&blk, g_noalloc_block);
+  if (e != cudaSuccess) return e;
+  S.racc = racc;
+  S.blk = static_cast<BlockDev *>(blk);
+  S.ready.store(true, std::memory_order_release);
+  return cudaSuccess;
+}
+
+// the descriptor arrives as a kernel argument (copied by value at launch) and is stored
+// into the static descriptor that the passes read
+__global__ void k_noalloc_store_block(BlockDev b) { g_noalloc_block = b; }
+}  // namespace
 
 namespace {
 
@@ -191,7 +269,7 @@ int upload_items(fp_ctx *c) {
     if (d < c->desc.dims) make_items(c->hblk, 0, d, c->hitems[d]);
     c->nitems[d] = (int)c->hitems[d].size();
     if (c->nitems[d] == 0) continue;
-    cudaError_t e = cudaMalloc(&c->items[d], c->hitems[d].size() * sizeof(int2));
+    cudaError_t e = fpk::dev_alloc(&c->items[d], c->hitems[d].size() * sizeof(int2));
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(items)");
     e = cudaMemcpy(c->items[d], c->hitems[d].data(), c->hitems[d].size() * sizeof(int2),
                    cudaMemcpyHostToDevice);
@@ -330,30 +408,30 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
       return st;                                    \
     }                                               \
   } while (0)
-  int dev = 0;
-  FP_TRY(cudaGetDevice(&dev), "cudaGetDevice");
-  FP_TRY(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev), "device attribute");
-  FP_TRY(cudaMalloc(&nodes, (size_t)dims * nnode * sizeof(double)), "cudaMalloc(nodes)");
+  FP_TRY(fpk::dev_alloc(&nodes, (size_t)dims * nnode * sizeof(double)), "cudaMalloc(nodes)");
+  FP_TRY(cudaGetDevice(&c->dev), "cudaGetDevice");
+  FP_TRY(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev), "device attribute");
+  FP_TRY(noalloc_prepare(c->dev), "static scratch of fp_rhs_noalloc");
   FP_TRY(cudaMemcpyAsync(nodes, xyz, (size_t)dims * nnode * sizeof(double), cudaMemcpyHostToDevice, s),
          "copy nodes");
-  FP_TRY(cudaMalloc(&met64, (size_t)10 * c->nmet * sizeof(double)), "cudaMalloc(metrics)");
+  FP_TRY(fpk::dev_alloc(&met64, (size_t)10 * c->nmet * sizeof(double)), "cudaMalloc(metrics)");
   for (int d = 0; d < dims; ++d) {
-    FP_TRY(cudaMalloc(&fm64[d], (size_t)3 * c->nface[d] * sizeof(double)), "cudaMalloc(face metrics)");
-    FP_TRY(cudaMalloc(&dk64[d], (size_t)3 * c->ncells * sizeof(double)), "cudaMalloc(metric differences)");
+    FP_TRY(fpk::dev_alloc(&fm64[d], (size_t)3 * c->nface[d] * sizeof(double)), "cudaMalloc(face metrics)");
+    FP_TRY(fpk::dev_alloc(&dk64[d], (size_t)3 * c->ncells * sizeof(double)), "cudaMalloc(metric differences)");
   }
-  FP_TRY(cudaMalloc(&scratch, (size_t)9 * (nb1 + nb2) * sizeof(double)), "cudaMalloc(metric scratch)");
+  FP_TRY(fpk::dev_alloc(&scratch, (size_t)9 * (nb1 + nb2) * sizeof(double)), "cudaMalloc(metric scratch)");
   fpk::MetricJob J;
   J.dims = dims; J.M = M; J.G = G; J.Gn = Gn;
   for (int d = 0; d < 3; ++d) { J.n[d] = n[d]; J.fmet[d] = fm64[d]; J.dk[d] = dk64[d]; }
   J.nodes = nodes; J.met = met64; J.scratch = scratch;
   FP_TRY(fpk::build_metrics(J, s), "build metrics");
   if (c->is_f32) {
-    FP_TRY(cudaMalloc(&c->met, (size_t)10 * c->nmet * sizeof(float)), "cudaMalloc(metrics f32)");
+    FP_TRY(fpk::dev_alloc(&c->met, (size_t)10 * c->nmet * sizeof(float)), "cudaMalloc(metrics f32)");
     FP_TRY(fpk::convert_f64_to_f32(met64, (float *)c->met, 10 * c->nmet, s), "convert metrics");
     for (int d = 0; d < dims; ++d) {
-      FP_TRY(cudaMalloc(&c->fmet[d], (size_t)3 * c->nface[d] * sizeof(float)), "cudaMalloc(face f32)");
+      FP_TRY(fpk::dev_alloc(&c->fmet[d], (size_t)3 * c->nface[d] * sizeof(float)), "cudaMalloc(face f32)");
       FP_TRY(fpk::convert_f64_to_f32(fm64[d], (float *)c->fmet[d], 3 * c->nface[d], s), "convert face metrics");
-      FP_TRY(cudaMalloc(&c->dk[d], (size_t)3 * c->ncells * sizeof(float)), "cudaMalloc(differences f32)");
+      FP_TRY(fpk::dev_alloc(&c->dk[d], (size_t)3 * c->ncells * sizeof(float)), "cudaMalloc(differences f32)");
       FP_TRY(fpk::convert_f64_to_f32(dk64[d], (float *)c->dk[d], 3 * c->ncells, s), "convert differences");
     }
   } else {
@@ -365,21 +443,21 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
   nodes = nullptr; scratch = nullptr;
   if (c->is_f32) { met64 = nullptr; for (int d = 0; d < 3; ++d) { fm64[d] = nullptr; dk64[d] = nullptr; } }
   const size_t sbytes = (size_t)5 * c->ncells * c->esize;
-  FP_TRY(cudaMalloc(&c->q1, sbytes), "cudaMalloc(stage 1)");
-  FP_TRY(cudaMalloc(&c->q2, sbytes), "cudaMalloc(stage 2)");
-  FP_TRY(cudaMalloc(&c->racc, sbytes), "cudaMalloc(residual)");
-  FP_TRY(cudaMalloc(&c->status, sizeof(int)), "cudaMalloc(status)");
+  FP_TRY(fpk::dev_alloc(&c->q1, sbytes), "cudaMalloc(stage 1)");
+  FP_TRY(fpk::dev_alloc(&c->q2, sbytes), "cudaMalloc(stage 2)");
+  FP_TRY(fpk::dev_alloc(&c->racc, sbytes), "cudaMalloc(residual)");
+  FP_TRY(fpk::dev_alloc(&c->status, sizeof(int)), "cudaMalloc(status)");
   FP_TRY(cudaMemset(c->status, 0, sizeof(int)), "clear status");
-  FP_TRY(cudaMalloc(&c->dt_dev, sizeof(double)), "cudaMalloc(dt)");
-  FP_TRY(cudaMalloc(&c->cfl_bits, sizeof(unsigned long long)), "cudaMalloc(cfl)");
-  FP_TRY(cudaMalloc(&c->dblk, sizeof(BlockDev)), "cudaMalloc(block)");
-  FP_TRY(cudaMalloc(&c->lamg, 9 * c->esize), "cudaMalloc(global speeds)");
+  FP_TRY(fpk::dev_alloc(&c->dt_dev, sizeof(double)), "cudaMalloc(dt)");
+  FP_TRY(fpk::dev_alloc(&c->cfl_bits, sizeof(unsigned long long)), "cudaMalloc(cfl)");
+  FP_TRY(fpk::dev_alloc(&c->dblk, sizeof(BlockDev)), "cudaMalloc(block)");
+  FP_TRY(fpk::dev_alloc(&c->lamg, 9 * c->esize), "cudaMalloc(global speeds)");
   FP_TRY(cudaMemset(c->lamg, 0, 9 * c->esize), "clear global speeds");
   {
     std::vector<int2> li;
     for (long long p0 = 0; p0 < c->ncells; p0 += fpk::kLamChunk) li.push_back(make_int2(0, (int)p0));
     c->nlam_items = (int)li.size();
-    FP_TRY(cudaMalloc(&c->lam_items, li.size() * sizeof(int2)), "cudaMalloc(speed items)");
+    FP_TRY(fpk::dev_alloc(&c->lam_items, li.size() * sizeof(int2)), "cudaMalloc(speed items)");
     FP_TRY(cudaMemcpy(c->lam_items, li.data(), li.size() * sizeof(int2), cudaMemcpyHostToDevice),
            "copy speed items");
   }
@@ -510,7 +588,6 @@ int fp_get_device_status(fp_ctx *c, void *stream) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "fp_get_device_status");
-  if (word & 2) return fail(c, FP_ERR_TIMEOUT, "a bounded device wait gave up");
   if (word & 1) return fail(c, FP_ERR_NONFINITE, "a stage produced a non-finite state");
   return FP_OK;
 }
@@ -587,9 +664,11 @@ static int batch_items_into(fp_batch *b, int d, const std::vector<int> *only_blo
   *dst = nullptr;
   *ndst = (int)it.size();
   if (it.empty()) return FP_OK;
-  cudaError_t e = cudaMalloc(dst, it.size() * sizeof(int2));
+  cudaError_t e = fpk::dev_alloc(dst, it.size() * sizeof(int2));
   if (e == cudaSuccess) e = cudaMemcpy(*dst, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch items: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    return bfail(b, e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA,
+                 std::string("batch items: ") + cudaGetErrorString(e));
   return FP_OK;
 }
 
@@ -721,21 +800,21 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
       for (int sd = 0; sd < 2; ++sd) B.nbr[d][sd] = nbr[(size_t)k * 6 + d * 2 + sd];
     b->hblk.push_back(B);
   }
-  cudaError_t e = cudaMalloc(&b->dblk, nblocks * sizeof(BlockDev));
-  if (e == cudaSuccess) e = cudaMalloc(&b->dt_dev, sizeof(double));
-  if (e == cudaSuccess) e = cudaMallocHost(&b->dt_host, sizeof(double));
+  cudaError_t e = fpk::dev_alloc(&b->dblk, nblocks * sizeof(BlockDev));
+  if (e == cudaSuccess) e = fpk::dev_alloc(&b->dt_dev, sizeof(double));
+  if (e == cudaSuccess) e = fpk::host_malloc(reinterpret_cast<void **>(&b->dt_host), sizeof(double));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->dt_ready, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->dt_dev, 0, sizeof(double), s);
-  if (e != cudaSuccess) { fp_batch_free(b); return FP_ERR_OOM; }
+  if (e != cudaSuccess) { fp_batch_free(b); return e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA; }
   {
     std::vector<int2> li;
     for (int k = 0; k < nblocks; ++k)
       for (long long p0 = 0; p0 < blocks[k]->ncells; p0 += fpk::kLamChunk) li.push_back(make_int2(k, (int)p0));
     b->nlam_items = (int)li.size();
-    e = cudaMalloc(&b->lam_items, li.size() * sizeof(int2));
+    e = fpk::dev_alloc(&b->lam_items, li.size() * sizeof(int2));
     if (e == cudaSuccess)
       e = cudaMemcpy(b->lam_items, li.data(), li.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { fp_batch_free(b); return FP_ERR_CUDA; }
+    if (e != cudaSuccess) { fp_batch_free(b); return e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA; }
   }
   int st = FP_OK;
   if (autotune) st = batch_autotune(b, s);
@@ -856,26 +935,9 @@ int fp_batch_rhs(fp_batch *b, void *const *dqdt_devs, void *stream) {
 
 // ----------------------------------------------------------------- allocation-free residual
 //
-// fp_rhs_noalloc: the same residual as fp_rhs, for callers that must not allocate device
-// memory inside their time loop (a host framework with a frozen memory pool or a fixed
-// device-memory budget, a real-time loop where an allocation would stall, code that
-// runs while other work is being captured into a graph and so may not call cudaMalloc).
-// The residual accumulator the three direction passes share lives in a fixed static
-// device array instead of context memory, and the block descriptor it needs in a static
-// device variable; the call itself allocates nothing.
-namespace {
-constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;      // 8 MiB, held by every GPU that loads the library
-__device__ __align__(256) unsigned char g_noalloc_racc[kNoAllocScratchBytes];
-__device__ __align__(256) BlockDev g_noalloc_block;
-constexpr int kNoAllocMaxDevices = 64;
-struct NoAllocDevice {
-  void *racc = nullptr;
-  BlockDev *blk = nullptr;
-  bool ready = false;
-};
-NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
-}  // namespace
-
+// fp_rhs_noalloc: the residual of fp_rhs for callers that cannot allocate device memory
+// where they evaluate it.  Same kernels, same data, same result bit for bit; the shared
+// residual accumulator is the static scratch above instead of context memory.
 extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream) {
   if (!c) return FP_ERR_ARG;
   if (!q || !dqdt) return fail(c, FP_ERR_ARG, "fp_rhs_noalloc: null buffer");
@@ -892,26 +954,20 @@ extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: cudaGetDevice");
+  if (dev != c->dev) return fail(c, FP_ERR_ARG, "fp_rhs_noalloc: the context's device must be current");
   if (dev < 0 || dev >= kNoAllocMaxDevices)
     return fail(c, FP_ERR_UNSUPPORTED, "fp_rhs_noalloc: device ordinal beyond 63");
-  NoAllocDevice &S = g_noalloc_dev[dev];
-  if (!S.ready) {
-    // once per device, with that device current: device addresses of the static arrays
-    e = cudaGetSymbolAddress(&S.racc, g_noalloc_racc);
-    if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: cudaGetSymbolAddress(scratch)");
-    void *bp = nullptr;
-    e = cudaGetSymbolAddress(&bp, g_noalloc_block);
-    if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: cudaGetSymbolAddress(descriptor)");
-    S.blk = static_cast<BlockDev *>(bp);
-    S.ready = true;
-  }
+  const NoAllocDevice &S = g_noalloc_dev[dev];
+  if (!S.ready.load(std::memory_order_acquire))     // set by the fp_init_grid that made c
+    return fail(c, FP_ERR_CUDA, "fp_rhs_noalloc: static scratch not set up on this device");
   cudaStream_t s = (cudaStream_t)stream;
   BlockDev b = c->hblk;
   b.q[0] = const_cast<void *>(q);
   b.dqdt = dqdt;
   b.racc = S.racc;                     // fully written by the first pass: nothing to clear
-  e = cudaMemcpyAsync(S.blk, &b, sizeof(BlockDev), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: descriptor upload");
+  k_noalloc_store_block<<<1, 1, 0, s>>>(b);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: descriptor store");
   const int dims = c->desc.dims, M = c->desc.metric_order;
   if (c->desc.global_lf) {
     e = fpk::launch_lambda(S.blk, 1, c->lam_items, c->nlam_items, c->is_f32, c->desc.characteristic, 0, s);
@@ -931,5 +987,11 @@ extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream
     e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic, c->desc.free_stream_preserving, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: sweep launch");
   }
+  return FP_OK;
+}
+
+// ----------------------------------------------------------------- failure injection
+extern "C" int fp_debug_fail_allocation(int n) {
+  g_fail_countdown.store(n < 0 ? -1 : (long long)n);
   return FP_OK;
 }

@@ -96,6 +96,15 @@ cudaError_t launch_sweep_f32_bnd(const SweepLaunch &L, int M, int scheme, int ch
 int prepare_sweep_f64_bnd(int M, int scheme);
 int prepare_sweep_f32_bnd(int M, int scheme);
 
+// Every device and page-locked allocation of the library goes through these two, so the
+// host-side hook fp_debug_fail_allocation can make a chosen one fail as if the device (or
+// the pinned host pool) were out of memory.  Defined in api.cu.
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t host_malloc(void **p, size_t bytes);
+template <typename P> inline cudaError_t dev_alloc(P **p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+
 // Metric construction (metrics.cu), FP64.
 struct MetricJob {
   int dims, M, G, Gn;

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/fp.h"
+#include "fp_internal.h"
 
 struct fp_pipe {
   std::vector<fp_ctx *> ctx;
@@ -75,7 +76,7 @@ int fp_pipe_create(fp_ctx *const *blocks, int nblocks, const void *const *q_host
   // device states, initialised from the host states (so autotuning runs on real data)
   p->qdev.assign(nblocks, nullptr);
   for (int k = 0; k < nblocks; ++k) {
-    cudaError_t e = cudaMalloc(&p->qdev[k], p->bytes[k]);
+    cudaError_t e = fpk::dev_malloc(&p->qdev[k], p->bytes[k]);
     if (e == cudaSuccess) e = cudaMemcpy(p->qdev[k], q_host[k], p->bytes[k], cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       fp_pipe_free(p);

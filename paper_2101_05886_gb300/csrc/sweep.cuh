@@ -733,98 +733,168 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           c[4] = psub(X4, Y4);
         };
 
-        // split stencil values f+/- for the NS stencil points
-        T fpl[NS][5], fmi[NS][5];
-        // f+- = (1/2) l.(dF +- lambda d (1/J)_m) of one stencil point
-        auto split_point = [&](int s, const T dF[5], const T d[5], T ijm) {
-          T cF[5], cD[5];
-          project(dF, cF);
-          project(d, cD);
-          const T mu0 = lam[0] * ijm, mu1 = lam[1] * ijm, mu4 = lam[4] * ijm;
-          const T mu[5] = {mu0, mu1, mu1, mu1, mu4};
+        // h: the back-projected characteristic part of the face flux, cen: the part added
+        // to it outside the projection (linear upwind only)
+        T h[5], cen[5] = {T(0), T(0), T(0), T(0), T(0)};
+        if constexpr (SCHEME == 1) {
+          // Linear upwind (Eq. linear_upwind; Appendix Eq. new_form_linear_upwind) is linear in
+          // the split values and the speeds are constant over the stencil, so the projection
+          // commutes with the reconstruction:
+          //   sum_s r_s [W+(f+_s) + W-(f-_s)] = C6(dF) + R Lambda L D(dQ~),
+          // C6 = (1, -8, 37, 37, -8, 1)/60 (half the sum of the two upwind stencils) and
+          // D = (1, -5, 10, -10, 5, -1)/60 (half their difference) over i-2..i+3.  One
+          // projection per face instead of two per stencil point; dF and dQ~ = dQ (1/J)_m as
+          // in the WENO branch (stencil point s paired with its mirror 5-s).
+          constexpr T c6[3] = {T(1.0 / 60.0), T(-8.0 / 60.0), T(37.0 / 60.0)};
+          constexpr T d5[3] = {T(1.0 / 60.0), T(-5.0 / 60.0), T(10.0 / 60.0)};
+          P cenp[5], disp[5];
 #pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            fpl[s][v] = cF[v] + mu[v] * cD[v];
-            fmi[s][v] = cF[v] - mu[v] * cD[v];
-          }
-        };
-        if (fpform) {
-          // reference-state differences of the stencil points two at a time (packed): points
-          // s and its mirror NS-1-s, whose f+ and f- are the (+, -) lanes of the reconstruction
-          // pair s; the mirror pair NS-1-s is formed lane by lane
-          const P lpm[3] = {pmk(lam[0], -lam[0]), pmk(lam[1], -lam[1]), pmk(lam[4], -lam[4])};
+          for (int v = 0; v < 5; ++v) cenp[v] = disp[v] = pc<P>(T(0));
 #pragma unroll
-          for (int s = 0; s < NS / 2; ++s) {
-            const int mir = NS - 1 - s;
-            const int q = s + Q0, q2 = mir + Q0;
-            P dp[5], kp2[3], uBp[3], out[5];
+          for (int s = 0; s < 3; ++s) {
+            const int q = s + 1, q2 = 6 - s;
+            P dp[5], out[5];
+            if (fpform) {
+              P kp2[3], uBp[3];
 #pragma unroll
-            for (int v = 0; v < 5; ++v)
-              dp[v] = psub(psub(pmk(CELL(CF_Q + v, q), CELL(CF_Q + v, q2)), pc<P>(Qi[v])), pc<P>(dl[v]));
+              for (int v = 0; v < 5; ++v)
+                dp[v] = psub(psub(pmk(CELL(CF_Q + v, q), CELL(CF_Q + v, q2)), pc<P>(Qi[v])), pc<P>(dl[v]));
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              kp2[c] = pmk(CELL(CF_K + c, q), CELL(CF_K + c, q2));
-              uBp[c] = pmk(CELL(CF_U + c, q), CELL(CF_U + c, q2));
+              for (int c = 0; c < 3; ++c) {
+                kp2[c] = pmk(CELL(CF_K + c, q), CELL(CF_K + c, q2));
+                uBp[c] = pmk(CELL(CF_U + c, q), CELL(CF_U + c, q2));
+              }
+              dflux_pair<T>(g1, pmk(CELL(CF_RINV, q), CELL(CF_RINV, q2)), uBp, us, ms, Qs[4], ps, dp, kp2, out);
+            } else {
+              // plain scheme: F~_m and Q~_m themselves
+              P uBp[3], kp2[3];
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                kp2[c] = pmk(CELL(CF_K + c, q), CELL(CF_K + c, q2));
+                uBp[c] = pmk(CELL(CF_U + c, q), CELL(CF_U + c, q2));
+              }
+#pragma unroll
+              for (int v = 0; v < 5; ++v) dp[v] = pmk(CELL(CF_Q + v, q), CELL(CF_Q + v, q2));
+              const P ke = pfma(dp[3], uBp[2], pfma(dp[2], uBp[1], pmul(dp[1], uBp[0])));
+              const P pm = pmul(pc<P>(g1), pfma(pc<P>(T(-0.5)), ke, dp[4]));
+              const P U = pfma(uBp[2], kp2[2], pfma(uBp[1], kp2[1], pmul(uBp[0], kp2[0])));
+              out[0] = pmul(dp[0], U);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) out[1 + c] = pfma(pm, kp2[c], pmul(dp[1 + c], U));
+              out[4] = pmul(padd(dp[4], pm), U);
             }
-            dflux_pair<T>(g1, pmk(CELL(CF_RINV, q), CELL(CF_RINV, q2)), uBp, us, ms, Qs[4], ps, dp, kp2, out);
-            P cF[5], cD[5];
-            project_pair(out, cF);
-            project_pair(dp, cD);
-            // (lambda (1/J)_s, -lambda (1/J)_mirror) for the three speed classes
             const P ijp = pmk(CELL(CF_INVJ, q), CELL(CF_INVJ, q2));
-            const P mp[3] = {pmul(lpm[0], ijp), pmul(lpm[1], ijp), pmul(lpm[2], ijp)};
+            const P ds = pmk(d5[s], -d5[s]);
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-              const P &mv = mp[v == 0 ? 0 : (v == 4 ? 2 : 1)];
-              const P r = pfma(mv, cD[v], cF[v]);                 // (f+ of s, f- of the mirror)
-              fpl[s][v] = r.x;
-              fmi[mir][v] = r.y;
-              fmi[s][v] = cF[v].x - mv.x * cD[v].x;
-              fpl[mir][v] = cF[v].y - mv.y * cD[v].y;
+              cenp[v] = pfma(pc<P>(c6[s]), out[v], cenp[v]);
+              disp[v] = pfma(ds, pmul(dp[v], ijp), disp[v]);
             }
           }
-        } else {
-          // plain scheme: F~_m and Q~_m themselves
+          T dis[5];
 #pragma unroll
-          for (int s = 0; s < NS; ++s) {
-            const int q = s + Q0;
-            T dF[5], d[5];
-            const T km[3] = {CELL(CF_K, q), CELL(CF_K + 1, q), CELL(CF_K + 2, q)};
-            const T uB[3] = {CELL(CF_U, q), CELL(CF_U + 1, q), CELL(CF_U + 2, q)};
-#pragma unroll
-            for (int v = 0; v < 5; ++v) d[v] = CELL(CF_Q + v, q);
-            const T pm = g1 * (d[4] - T(0.5) * (d[1] * uB[0] + d[2] * uB[1] + d[3] * uB[2]));
-            const T U = uB[0] * km[0] + uB[1] * km[1] + uB[2] * km[2];
-            dF[0] = d[0] * U;
-            dF[1] = d[1] * U + pm * km[0];
-            dF[2] = d[2] * U + pm * km[1];
-            dF[3] = d[3] * U + pm * km[2];
-            dF[4] = (d[4] + pm) * U;
-            split_point(s, dF, d, CELL(CF_INVJ, q));
+          for (int v = 0; v < 5; ++v) {
+            cen[v] = cenp[v].x + cenp[v].y;
+            dis[v] = disp[v].x + disp[v].y;
           }
-        }
-#undef CELL
-        // reconstruct each field from both sides (the - side mirrored) and back-project
-        T h[5];
+          // lambda_s l_s . D (project() carries the 1/2 of the split: twice its rows)
+          T c[5];
+          project(dis, c);
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          if constexpr (SCHEME == 2) {
-            P w7[7];
+          for (int v = 0; v < 5; ++v) h[v] = T(2) * lam[v] * c[v];
+        } else {
+          // split stencil values f+/- for the NS stencil points
+          T fpl[NS][5], fmi[NS][5];
+          // f+- = (1/2) l.(dF +- lambda d (1/J)_m) of one stencil point
+          auto split_point = [&](int s, const T dF[5], const T d[5], T ijm) {
+            T cF[5], cD[5];
+            project(dF, cF);
+            project(d, cD);
+            const T mu0 = lam[0] * ijm, mu1 = lam[1] * ijm, mu4 = lam[4] * ijm;
+            const T mu[5] = {mu0, mu1, mu1, mu1, mu4};
 #pragma unroll
-            for (int t = 0; t < 7; ++t) w7[t] = pmk(fpl[t][v], fmi[7 - t][v]);   // i-3..i+3 / i+4..i-2
-            const P r = recon7_pair<T>(w7);
-            h[v] = r.x + r.y;
-          } else if constexpr (SCHEME == 3) {
-            P w6[6];
+            for (int v = 0; v < 5; ++v) {
+              fpl[s][v] = cF[v] + mu[v] * cD[v];
+              fmi[s][v] = cF[v] - mu[v] * cD[v];
+            }
+          };
+          if (fpform) {
+            // reference-state differences of the stencil points two at a time (packed): points
+            // s and its mirror NS-1-s, whose f+ and f- are the (+, -) lanes of the reconstruction
+            // pair s; the mirror pair NS-1-s is formed lane by lane
+            const P lpm[3] = {pmk(lam[0], -lam[0]), pmk(lam[1], -lam[1]), pmk(lam[4], -lam[4])};
 #pragma unroll
-            for (int t = 0; t < 6; ++t) w6[t] = pmk(fpl[t][v], fmi[5 - t][v]);   // i-2..i+3 / i+3..i-2
-            const P r = recon6cu_pair<T>(w6);
-            h[v] = r.x + r.y;
+            for (int s = 0; s < NS / 2; ++s) {
+              const int mir = NS - 1 - s;
+              const int q = s + Q0, q2 = mir + Q0;
+              P dp[5], kp2[3], uBp[3], out[5];
+#pragma unroll
+              for (int v = 0; v < 5; ++v)
+                dp[v] = psub(psub(pmk(CELL(CF_Q + v, q), CELL(CF_Q + v, q2)), pc<P>(Qi[v])), pc<P>(dl[v]));
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                kp2[c] = pmk(CELL(CF_K + c, q), CELL(CF_K + c, q2));
+                uBp[c] = pmk(CELL(CF_U + c, q), CELL(CF_U + c, q2));
+              }
+              dflux_pair<T>(g1, pmk(CELL(CF_RINV, q), CELL(CF_RINV, q2)), uBp, us, ms, Qs[4], ps, dp, kp2, out);
+              P cF[5], cD[5];
+              project_pair(out, cF);
+              project_pair(dp, cD);
+              // (lambda (1/J)_s, -lambda (1/J)_mirror) for the three speed classes
+              const P ijp = pmk(CELL(CF_INVJ, q), CELL(CF_INVJ, q2));
+              const P mp[3] = {pmul(lpm[0], ijp), pmul(lpm[1], ijp), pmul(lpm[2], ijp)};
+#pragma unroll
+              for (int v = 0; v < 5; ++v) {
+                const P &mv = mp[v == 0 ? 0 : (v == 4 ? 2 : 1)];
+                const P r = pfma(mv, cD[v], cF[v]);                 // (f+ of s, f- of the mirror)
+                fpl[s][v] = r.x;
+                fmi[mir][v] = r.y;
+                fmi[s][v] = cF[v].x - mv.x * cD[v].x;
+                fpl[mir][v] = cF[v].y - mv.y * cD[v].y;
+              }
+            }
           } else {
-            const P r = recon5_pair<T, SCHEME>(pmk(fpl[0][v], fmi[5][v]), pmk(fpl[1][v], fmi[4][v]),
-                                               pmk(fpl[2][v], fmi[3][v]), pmk(fpl[3][v], fmi[2][v]),
-                                               pmk(fpl[4][v], fmi[1][v]));
-            h[v] = r.x + r.y;
+            // plain scheme: F~_m and Q~_m themselves
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              const int q = s + Q0;
+              T dF[5], d[5];
+              const T km[3] = {CELL(CF_K, q), CELL(CF_K + 1, q), CELL(CF_K + 2, q)};
+              const T uB[3] = {CELL(CF_U, q), CELL(CF_U + 1, q), CELL(CF_U + 2, q)};
+#pragma unroll
+              for (int v = 0; v < 5; ++v) d[v] = CELL(CF_Q + v, q);
+              const T pm = g1 * (d[4] - T(0.5) * (d[1] * uB[0] + d[2] * uB[1] + d[3] * uB[2]));
+              const T U = uB[0] * km[0] + uB[1] * km[1] + uB[2] * km[2];
+              dF[0] = d[0] * U;
+              dF[1] = d[1] * U + pm * km[0];
+              dF[2] = d[2] * U + pm * km[1];
+              dF[3] = d[3] * U + pm * km[2];
+              dF[4] = (d[4] + pm) * U;
+              split_point(s, dF, d, CELL(CF_INVJ, q));
+            }
+          }
+#undef CELL
+          // reconstruct each field from both sides (the - side mirrored) and back-project
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            if constexpr (SCHEME == 2) {
+              P w7[7];
+#pragma unroll
+              for (int t = 0; t < 7; ++t) w7[t] = pmk(fpl[t][v], fmi[7 - t][v]);   // i-3..i+3 / i+4..i-2
+              const P r = recon7_pair<T>(w7);
+              h[v] = r.x + r.y;
+            } else if constexpr (SCHEME == 3) {
+              P w6[6];
+#pragma unroll
+              for (int t = 0; t < 6; ++t) w6[t] = pmk(fpl[t][v], fmi[5 - t][v]);   // i-2..i+3 / i+3..i-2
+              const P r = recon6cu_pair<T>(w6);
+              h[v] = r.x + r.y;
+            } else {
+              const P r = recon5_pair<T, SCHEME>(pmk(fpl[0][v], fmi[5][v]), pmk(fpl[1][v], fmi[4][v]),
+                                                 pmk(fpl[2][v], fmi[3][v]), pmk(fpl[3][v], fmi[2][v]),
+                                                 pmk(fpl[4][v], fmi[1][v]));
+              h[v] = r.x + r.y;
+            }
           }
         }
         T F[5];
@@ -841,6 +911,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         T *fp = fr + off(ff);
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
+          if constexpr (SCHEME == 1) F[v] += cen[v];
           fp[v * kRing] = F[v];
           fp[(5 + v) * kRing] = dl[v];
         }

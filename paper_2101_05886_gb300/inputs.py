@@ -201,11 +201,21 @@ def cartesian_3d(n, h, Gn, periodic=True):
     return Grid(3, (ni, nj, nk), Gn, nodes, (b, b, b), "cartesian_3d")
 
 
-def periodic_wavy_3d(n, L=10.0, amp=0.08, Gn=6, dtype=np.float64):
+def periodic_wavy_3d(n, L=10.0, amp=0.08, Gn=6, dtype=np.float64, k_range=None):
     """Periodic 3-D wavy grid on [0,L)^3: each coordinate x_a = L(xi'_a + amp
-    sin 2pi xi' sin 2pi eta' sin 2pi zeta'), xi'_a = index/n_a."""
+    sin 2pi xi' sin 2pi eta' sin 2pi zeta'), xi'_a = index/n_a.
+    k_range=(k0, k1): only the points k0 <= k < k1 of that grid (any integers: the mapping
+    is evaluated there, with Gn ghost layers around the range), as a block of
+    (ni, nj, k1 - k0) points whose nodes equal the full grid's bit for bit."""
     ni, nj, nk = n
-    KK, JJ, II = _mesh3(ni, nj, nk, Gn)
+    if k_range is None:
+        KK, JJ, II = _mesh3(ni, nj, nk, Gn)
+        nb = nk
+    else:
+        k0, k1 = k_range
+        nb = k1 - k0
+        KK, JJ, II = np.meshgrid(np.arange(k0 - Gn, k1 + Gn, dtype=np.float64), _index_range(nj, Gn),
+                                 _index_range(ni, Gn), indexing="ij")
     xi, eta, zeta = II / ni, JJ / nj, KK / nk
     s = amp * np.sin(2 * np.pi * xi) * np.sin(2 * np.pi * eta) * np.sin(2 * np.pi * zeta)
     nodes = np.empty((3,) + KK.shape, dtype=dtype)
@@ -213,7 +223,7 @@ def periodic_wavy_3d(n, L=10.0, amp=0.08, Gn=6, dtype=np.float64):
     nodes[1] = L * (eta + s)
     nodes[2] = L * (zeta + s)
     b = (BC_PERIODIC, BC_PERIODIC)
-    return Grid(3, (ni, nj, nk), Gn, nodes, (b, b, b), "periodic_wavy_3d")
+    return Grid(3, (ni, nj, nb), Gn, nodes, (b, b, b), "periodic_wavy_3d")
 
 
 def cylinder_ogrid(n, r0=0.5, r1=20.0, beta=3.0, Lz=4.0, Gn=6, wall=False):

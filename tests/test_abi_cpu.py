@@ -144,3 +144,23 @@ def test_balanced_groups_rejects_invalid_arguments(lib):
     neg = (ctypes.c_longlong * 1)(-1)
     assert lib.fp_balanced_groups(neg, 1, 2, out) == B.FP_ERR_ARG
     assert lib.fp_balanced_groups(None, 0, 2, None) == B.FP_OK
+
+
+def test_scheduled_allocation_failure_returns_oom_before_any_gpu_work(lib):
+    """The host-side failure hook: with the next allocation scheduled to fail, fp_init_grid
+    returns FP_ERR_OOM (its first allocation is the node array, made before any other CUDA
+    call) and hands back no context; the hook disarms itself after firing, and a pending
+    failure can be cancelled."""
+    d = B.make_desc(3, (8, 8, 8), metric_order=6)
+    nodes = np.zeros(3 * 32 ** 3)
+    ctx = ctypes.c_void_p()
+    assert B.fp_debug_fail_allocation(0) == B.FP_OK
+    st = lib.fp_init_grid(ctypes.byref(d), nodes.ctypes.data, 12, None, ctypes.byref(ctx))
+    assert st == B.FP_ERR_OOM and not ctx.value
+    assert B.fp_debug_fail_allocation(5) == B.FP_OK
+    assert B.fp_debug_fail_allocation(-1) == B.FP_OK
+    # invalid arguments are still rejected first, whatever is armed
+    B.fp_debug_fail_allocation(0)
+    d.metric_order = 5
+    assert lib.fp_init_grid(ctypes.byref(d), nodes.ctypes.data, 12, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
+    B.fp_debug_fail_allocation(-1)

@@ -8,7 +8,8 @@ torch = pytest.importorskip("torch")
 
 import oracle as O
 from paper_2101_05886_gb300 import inputs as I
-from tests.helpers import oracle_subbox_dqdt, rel_err, ulp_sensitivity
+from tests.helpers import (Parity, f32, residual_err, rhs_err, state_err, subbox_err, subbox_sensitivity,
+                           ulp_sensitivity)
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +60,10 @@ PARITY_CASES = [
     ("2d_ragged", 8, 0, 1, 1), ("3d_vortex", 6, 0, 1, 1), ("3d_vortex", 2, 1, 1, 1),
     ("3d_vortex", 8, 0, 1, 1), ("3d_vortex", 6, 0, 0, 1), ("3d_vortex", 6, 0, 1, 0),
     ("3d_ogrid", 6, 0, 1, 1), ("3d_ogrid", 4, 1, 1, 1), ("3d_min", 6, 0, 1, 1), ("3d_min", 8, 1, 1, 1),
+    # linear upwind (projection after the linear reconstruction): M6 characteristic and
+    # component-wise, the plain scheme, and a ragged 2-D block
+    ("3d_vortex", 6, 1, 1, 1), ("3d_vortex", 6, 1, 0, 1), ("3d_ogrid", 6, 1, 1, 0), ("3d_ogrid", 8, 1, 0, 1),
+    ("2d_config1", 6, 1, 1, 1), ("2d_ragged", 6, 1, 1, 1),
 ]
 
 
@@ -100,15 +105,28 @@ def test_face_metrics_are_order_M_midpoint_values(M):
     blk.close()
 
 
+def _fp64_tol(cfg, met, q):
+    """FP64 bound: 1e-12, or twice the oracle's own response to one-ulp input changes where
+    that is larger.  On the z-extruded vortex the rho w residual is a cancellation between the
+    three directions' pressure terms (about 2 % of each), and the oracle's per-field
+    Lax-Friedrichs split cancels too, so the oracle itself moves by up to 1.6e-12 of this
+    metric under one-ulp input changes there; a linear-upwind evaluation that projects after
+    reconstructing (no such cancellation) differs from it by about that much.  The bound
+    never exceeds 5e-12."""
+    tol = max(1e-12, 2.0 * ulp_sensitivity(cfg, met, q))
+    assert tol <= 5e-12, tol
+    return tol
+
+
 @pytest.mark.parametrize("name,M,scheme,charwise,fp", PARITY_CASES)
 def test_rhs_parity_fp64(name, M, scheme, charwise, fp):
     g, qinf, q = _case(name, M)
     blk = Block(g, metric_order=M, scheme=scheme, fp=fp, characteristic=charwise, precision=F64, q_inf=qinf)
     dq = blk.rhs(blk.to_device(q)).cpu().numpy()
     cfg = O.cfg_for(g, M=M, scheme=scheme, fp=fp, charwise=charwise, qinf=qinf)
-    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q)
-    errs = rel_err(dq, dqo, per_component=True)
-    assert max(errs) <= 1e-12, errs
+    met = O.metrics(cfg, g.nodes, g.Gn)
+    errs = rhs_err(dq, cfg, met, q, per_component=True)
+    assert max(errs) <= _fp64_tol(cfg, met, q), errs
     blk.close()
 
 
@@ -125,7 +143,7 @@ def test_rk3_step_parity_fp64(name, M, scheme):
         blk.rk3_step(qd, dt)
         qo = O.rk3_step(cfg, met, qo, dt)
     # compare the change over the steps, scaled by its size
-    assert rel_err(qd.cpu().numpy() - q, qo - q) <= 1e-11
+    assert state_err(qd.cpu().numpy() - q, qo - q) <= 1e-11
     assert blk.status() == B.FP_OK
     blk.close()
 
@@ -139,38 +157,36 @@ def test_cfl_dt_parity():
     blk.close()
 
 
-@pytest.mark.parametrize("name,M,scheme", [("2d_vortex", 6, 0), ("3d_vortex", 6, 0), ("3d_vortex", 2, 1),
-                                           ("3d_ogrid", 6, 0)])
-def test_rhs_parity_fp32_mixed(name, M, scheme):
+@pytest.mark.parametrize("name,M,scheme,charwise", [("2d_vortex", 6, 0, 1), ("3d_vortex", 6, 0, 1), ("3d_vortex", 2, 1, 1),
+                                                    ("3d_ogrid", 6, 0, 1), ("3d_vortex", 6, 1, 1), ("3d_ogrid", 6, 1, 1),
+                                                    ("3d_vortex", 6, 1, 0), ("2d_config1", 6, 1, 1)])
+def test_rhs_parity_fp32_mixed(name, M, scheme, charwise):
     g, qinf, q = _case(name, M)
-    q32 = q.astype(np.float32).astype(np.float64)     # the same (float-representable) input on both sides
-    blk = Block(g, metric_order=M, scheme=scheme, precision=F32, q_inf=qinf)
+    q32, qinf = f32(q), f32(qinf)     # the same (float-representable) inputs on both sides
+    blk = Block(g, metric_order=M, scheme=scheme, characteristic=charwise, precision=F32, q_inf=qinf)
     dq = blk.rhs(blk.to_device(q32)).cpu().numpy()
-    cfg = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf)
-    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q32)
-    errs = rel_err(dq, dqo, per_component=True)
+    cfg = O.cfg_for(g, M=M, scheme=scheme, charwise=charwise, qinf=qinf)
+    errs = rhs_err(dq, cfg, O.metrics(cfg, g.nodes, g.Gn), q32, per_component=True)
     assert max(errs) <= 1e-5, errs
     blk.close()
 
 
-def test_mach3_small_perturbation_fp32_error_scales_with_the_perturbation():
-    """FP32 error is relative to the residual of the perturbation (the FP32 form
-    works on state differences), not to the full flux: with a 1e-3 perturbation
-    of a Mach 3 stream the residual is about 1e-3 of the flux scale, so an error
-    proportional to the flux would be near 1e-4; the measured error is 1.5e-5,
-    set by the cancellation between the two split reconstructions."""
+def test_mach3_small_perturbation_fp32_error_within_1e5():
+    """The headline workload's flow (Mach 3 stream, 1e-3 smooth perturbation) on an O-grid
+    with a far-field side: FP32 within 1e-5 of the FP64 oracle.  This residual is about
+    1e-4 of the flux scale, so a far-field state that differed between the two sides by
+    one float rounding (6e-8 relative) would alone move it by ~1.4e-5; both sides take
+    the float-rounded q_inf, as they take the float-rounded state."""
     M = 6
     Gn = O.node_ghost(M)
     g = I.cylinder_ogrid((24, 18, 10), Lz=3.0, Gn=Gn)
-    qinf = I.uniform_qinf(3.0, 0.0)
-    q = I.perturbed_state(g, qinf, amp=1e-3, seed=2)
-    q32 = q.astype(np.float32).astype(np.float64)
+    qinf = f32(I.uniform_qinf(3.0, 0.0))
+    q = f32(I.perturbed_state(g, qinf, amp=1e-3, seed=2))
     blk = Block(g, metric_order=M, precision=F32, q_inf=qinf)
-    dq = blk.rhs(blk.to_device(q32)).cpu().numpy()
+    dq = blk.rhs(blk.to_device(q)).cpu().numpy()
     cfg = O.cfg_for(g, M=M, qinf=qinf)
-    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q32)
-    errs = rel_err(dq, dqo, per_component=True)
-    assert max(errs) <= 3e-5, errs
+    errs = rhs_err(dq, cfg, O.metrics(cfg, g.nodes, g.Gn), q, per_component=True)
+    assert max(errs) <= 1e-5, errs
     blk.close()
 
 
@@ -290,7 +306,7 @@ def test_batch_rk3_parity_with_oracle_fp64():
     for g, s, q in zip(grids, states, q0):
         cfg = O.cfg_for(g, M=4, qinf=qinf)
         qo = O.rk3_step(cfg, O.metrics(cfg, g.nodes, g.Gn), q, dt)
-        assert rel_err(s.cpu().numpy() - q, qo - q) <= 1e-11
+        assert state_err(s.cpu().numpy() - q, qo - q) <= 1e-11
     batch.close()
     for b in blocks:
         b.close()
@@ -311,24 +327,28 @@ def test_nonfinite_state_is_reported_not_faulted():
 @pytest.mark.parametrize("precision,tol", [(F32, 1e-5), (F64, 1e-12)])
 def test_full_size_256cubed_sampled_parity(precision, tol):
     """The 256^3 wavy-grid vortex case at full size: GPU dQ/dt compared with the
-    oracle on interior sub-boxes."""
+    oracle on interior sub-boxes (in the vortex core, and in the nearly uniform stream
+    where the residual is below the parity floor).  In FP64 the bound is that of
+    _fp64_tol: on these sub-boxes the floor tau binds on every component but rho u and the
+    oracle's own one-ulp response reaches 1.2e-12 to 2.8e-12 of this metric."""
     M = 6
     g = I.periodic_wavy_3d((256, 256, 256), L=10.0, amp=0.08, Gn=O.node_ghost(M))
     qinf = I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0)
     q = I.vortex_3d(g, mach=0.8, eps=5.0, L=10.0)
     if precision == F32:
-        q = q.astype(np.float32).astype(np.float64)
+        q, qinf = f32(q), f32(qinf)
     blk = Block(g, metric_order=M, precision=precision, q_inf=qinf)
     dq = blk.rhs(blk.to_device(q))
     for lo in ((120, 122, 7), (3, 60, 200), (240, 5, 100)):
         lo = np.array(lo)
         size = np.array((8, 8, 8))
-        ref = oracle_subbox_dqdt(g, q, M, lo, size, qinf=qinf)
         got = dq[:, lo[2]:lo[2] + 8, lo[1]:lo[1] + 8, lo[0]:lo[0] + 8].cpu().numpy()
-        full_scale = dq.abs().amax(dim=(1, 2, 3)).cpu().numpy()
-        full_scale = np.maximum(full_scale, 1e-1 * full_scale.max())
-        err = max(np.abs(got[c] - ref[c]).max() / full_scale[c] for c in range(5))
-        assert err <= tol, (lo, err, [np.abs(got[c] - ref[c]).max() / full_scale[c] for c in range(5)])
+        err = subbox_err(got, g, q, M, lo, size, qinf=qinf)
+        bound = tol
+        if precision == F64:
+            bound = max(tol, 2.0 * subbox_sensitivity(g, q, M, lo, size, qinf=qinf))
+            assert bound <= 6e-12, bound
+        assert err <= bound, (lo, err, bound)
     blk.close()
 
 
@@ -338,17 +358,20 @@ def test_full_size_256cubed_sampled_parity(precision, tol):
 def test_global_lax_friedrichs_parity(name, M, scheme, precision, tol):
     g, qinf, q = _case(name, M)
     if precision == F32:
-        q = q.astype(np.float32).astype(np.float64)
+        q, qinf = f32(q), f32(qinf)
     blk = Block(g, metric_order=M, scheme=scheme, precision=precision, q_inf=qinf, global_lf=1)
     dq = blk.rhs(blk.to_device(q)).cpu().numpy()
     cfg = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf, global_lf=1)
-    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q)
-    errs = rel_err(dq, dqo, per_component=True)
+    met = O.metrics(cfg, g.nodes, g.Gn)
+    P = Parity(cfg, met, q)
+    errs = P.err(dq, per_component=True)
+    if precision == F64:
+        tol = _fp64_tol(cfg, met, q)
     assert max(errs) <= tol, errs
     # the global splitting is more dissipative: it differs from the local one
     cfl = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf)
-    _, dql = O.rhs(cfl, O.metrics(cfl, g.nodes, g.Gn), q)
-    assert rel_err(dql, dqo) > 1e-6
+    Rl, _ = O.rhs(cfl, met, q)
+    assert residual_err(Rl, P.R, P.tau) > 1e-6
     blk.close()
 
 
@@ -364,16 +387,15 @@ def test_shock_on_randomised_grid_parity_and_no_overshoot(frac):
     blk = Block(g, metric_order=M, precision=F64, q_inf=qinf, global_lf=1)
     cfg = O.cfg_for(g, M=M, qinf=qinf, global_lf=1)
     met = O.metrics(cfg, g.nodes, g.Gn)
-    _, dqo = O.rhs(cfg, met, q)
     qd = blk.to_device(q)
-    assert rel_err(blk.rhs(qd).cpu().numpy(), dqo) <= 1e-12
+    assert rhs_err(blk.rhs(qd).cpu().numpy(), cfg, met, q) <= _fp64_tol(cfg, met, q)
     dt = 0.5 * O.cfl_dt(cfg, met, q, 0.5)
     qo = q.copy()
     for _ in range(10):
         blk.rk3_step(qd, dt)
         qo = O.rk3_step(cfg, met, qo, dt)
     qg = qd.cpu().numpy()
-    assert rel_err(qg - q, qo - q) <= 1e-10
+    assert state_err(qg - q, qo - q) <= 1e-10
     rho = qg[0]
     r1, r2 = q[0].min(), q[0].max()
     assert rho.min() > r1 - 0.05 * (r2 - r1) and rho.max() < r2 + 0.05 * (r2 - r1)
@@ -404,8 +426,7 @@ def test_weno7_rhs_parity_fp64(name, M, charwise, fp):
     dq = blk.rhs(blk.to_device(q)).cpu().numpy()
     cfg = O.cfg_for(g, M=M, scheme=W7, fp=fp, charwise=charwise, qinf=qinf)
     met = O.metrics(cfg, g.nodes, g.Gn)
-    _, dqo = O.rhs(cfg, met, q)
-    errs = rel_err(dq, dqo, per_component=True)
+    errs = rhs_err(dq, cfg, met, q, per_component=True)
     tol = _weno7_tol(cfg, met, q)
     assert tol <= 1e-10
     assert max(errs) <= tol, (errs, tol)
@@ -416,12 +437,11 @@ def test_weno7_rhs_parity_fp64(name, M, charwise, fp):
 def test_weno7_rhs_parity_fp32_mixed(name, M):
     W7 = B.FP_WENO7_JS
     g, qinf, q = _case(name, M, W7)
-    q32 = q.astype(np.float32).astype(np.float64)
+    q32, qinf = f32(q), f32(qinf)
     blk = Block(g, metric_order=M, scheme=W7, precision=F32, q_inf=qinf)
     dq = blk.rhs(blk.to_device(q32)).cpu().numpy()
     cfg = O.cfg_for(g, M=M, scheme=W7, qinf=qinf)
-    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q32)
-    errs = rel_err(dq, dqo, per_component=True)
+    errs = rhs_err(dq, cfg, O.metrics(cfg, g.nodes, g.Gn), q32, per_component=True)
     assert max(errs) <= 1e-5, errs
     blk.close()
 
@@ -433,16 +453,15 @@ def test_weno7_rk3_and_global_lf_parity_fp64():
     met = O.metrics(cfg, g.nodes, g.Gn)
     blk = Block(g, metric_order=8, scheme=W7, precision=F64, q_inf=qinf, global_lf=1)
     dq = blk.rhs(blk.to_device(q)).cpu().numpy()
-    _, dqo = O.rhs(cfg, met, q)
     tol = _weno7_tol(cfg, met, q)
-    assert max(rel_err(dq, dqo, per_component=True)) <= tol
+    assert rhs_err(dq, cfg, met, q) <= tol
     dt = 0.5 * O.cfl_dt(cfg, met, q, 0.5)
     qd = blk.to_device(q)
     qo = q.copy()
     for _ in range(2):
         blk.rk3_step(qd, dt)
         qo = O.rk3_step(cfg, met, qo, dt)
-    assert rel_err(qd.cpu().numpy() - q, qo - q) <= max(1e-11, tol)
+    assert state_err(qd.cpu().numpy() - q, qo - q) <= max(1e-11, tol)
     assert blk.status() == B.FP_OK
     blk.close()
 
@@ -533,12 +552,12 @@ def _wall_cut_case(name, M, scheme=0):
 
 WALL_CUT_CASES = [
     ("channel_walls", 6, 0, F64, 1e-12), ("channel_walls", 8, 2, F64, None), ("channel_walls", 2, 1, F32, 1e-5),
-    ("channel_walls_T", 6, 0, F64, 1e-12), ("ogrid_wall", 6, 0, F64, 1e-12), ("ogrid_wall", 4, 0, F32, 3e-5),
+    ("channel_walls_T", 6, 0, F64, 1e-12), ("ogrid_wall", 6, 0, F64, 1e-12), ("ogrid_wall", 4, 0, F32, 1e-5),
     ("parabolic_cut", 6, 0, F64, 1e-12), ("parabolic_cut", 6, 1, F32, 1e-5), ("parabolic_plate", 4, 0, F64, 1e-12),
     ("cgrid_wing", 6, 0, F64, 1e-12), ("cgrid_wing", 6, 0, F32, 1e-5),
     # the boundary rules combined with the other options of the sweep
     ("ogrid_wall", 6, 0, F64, 1e-12, 1), ("parabolic_cut", 6, 0, F32, 1e-5, 1), ("cgrid_wing", 4, 1, F64, 1e-12, 1),
-    ("parabolic_cut", 6, 3, F64, None), ("cgrid_wing", 6, 2, F64, None), ("ogrid_wall", 6, 3, F32, 3e-5),
+    ("parabolic_cut", 6, 3, F64, None), ("cgrid_wing", 6, 2, F64, None), ("ogrid_wall", 6, 3, F32, 1e-5),
 ]
 
 
@@ -551,16 +570,17 @@ def test_wall_and_cut_parity(case):
     glf = case[5] if len(case) > 5 else 0
     g, qinf, q = _wall_cut_case(name, M, scheme)
     if precision == F32:
-        q = q.astype(np.float32).astype(np.float64)
+        q, qinf = f32(q), f32(qinf)
     blk = Block(g, metric_order=M, scheme=scheme, precision=precision, q_inf=qinf, global_lf=glf)
     dq = blk.rhs(blk.to_device(q)).cpu().numpy()
     cfg = O.cfg_for(g, M=M, scheme=scheme, qinf=qinf, global_lf=glf)
     met = O.metrics(cfg, g.nodes, g.Gn)
-    _, dqo = O.rhs(cfg, met, q)
     if tol is None:                              # WENO7 / WENOCU6 in FP64: the conditioning bound
         tol = _weno7_tol(cfg, met, q)
         assert tol <= 1e-5
-    errs = rel_err(dq, dqo, per_component=True)
+    elif precision == F64:
+        tol = _fp64_tol(cfg, met, q)
+    errs = rhs_err(dq, cfg, met, q, per_component=True)
     assert max(errs) <= tol, (errs, tol)
     blk.close()
 
@@ -593,7 +613,7 @@ def test_wall_and_cut_rk3_parity_and_batch_bitwise():
     for a, r, (c, m, q) in zip(qs, refs, cfgs):
         assert torch.equal(a, r)
         qo = O.rk3_step(c, m, O.rk3_step(c, m, q, dt), dt)
-        assert rel_err(a.cpu().numpy() - q, qo - q) <= 1e-11
+        assert state_err(a.cpu().numpy() - q, qo - q) <= 1e-11
     bat.close()
     for b in singles + batched:
         b.close()
@@ -611,7 +631,7 @@ def _split_case(direction, sizes, precision, wall=False):
         qinf = I.uniform_qinf(0.8, 0.0, rho=1.0, p=1.0)
     q = I.random_smooth_state(g, qinf, amp=0.05, seed=21)
     if precision == F32:
-        q = q.astype(np.float32).astype(np.float64)
+        q, qinf = f32(q), f32(qinf)
     parts, links = I.split_grid(g, direction, sizes)
     qparts = I.split_state(q, direction, sizes)
     whole = Block(g, metric_order=M, precision=precision, q_inf=qinf)
@@ -638,24 +658,24 @@ def test_linked_blocks_equal_the_unsplit_block(direction, sizes, precision, wall
     outs = bat.rhs([torch.empty_like(s) for s in states])
     torch.cuda.synchronize()
     got = np.concatenate([o.cpu().numpy() for o in outs], axis=ax)
+    cfg = O.cfg_for(g, M=6, qinf=qinf)
+    P_met = O.metrics(cfg, g.nodes, g.Gn)
+    P = Parity(cfg, P_met, q)
     tol = 1e-14 if precision == F64 else 1e-6
-    assert rel_err(got, ref) <= tol
+    assert residual_err(-got * P.invJ, -ref * P.invJ, P.tau) <= tol
     for ib, (b, p) in enumerate(zip(blocks, parts)):   # the linked ghost nodes give the same metrics
         a0 = sum(sizes[:ib])
         sl = [slice(None)] * 4
         sl[ax] = slice(a0, a0 + p.n[direction] + 2 * whole.G)
         assert np.array_equal(b.metrics(), whole.metrics()[tuple(sl)])
-    if precision == F64:
-        cfg = O.cfg_for(g, M=6, qinf=qinf)
-        _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q)
-        assert max(rel_err(got, dqo, per_component=True)) <= 1e-12
+    assert P.err(got) <= (_fp64_tol(cfg, P_met, q) if precision == F64 else 1e-5)
     dt = 0.5 * whole.cfl_dt(qd, 0.5)
     for _ in range(2):
         bat.rk3_step(dt)
         whole.rk3_step(qd, dt)
     torch.cuda.synchronize()
     stepped = np.concatenate([s.cpu().numpy() for s in states], axis=ax)
-    assert rel_err(stepped - q, qd.cpu().numpy() - q) <= (1e-12 if precision == F64 else 1e-5)
+    assert state_err(stepped - q, qd.cpu().numpy() - q) <= (1e-12 if precision == F64 else 1e-5)
     assert all(b.status() == B.FP_OK for b in blocks)
     bat.close()
     for b in blocks + [whole]:
@@ -697,11 +717,36 @@ def test_wenocu6_rhs_parity_fp64(name, M, charwise, fp):
     dq = blk.rhs(blk.to_device(q)).cpu().numpy()
     cfg = O.cfg_for(g, M=M, scheme=CU, fp=fp, charwise=charwise, qinf=qinf)
     met = O.metrics(cfg, g.nodes, g.Gn)
-    _, dqo = O.rhs(cfg, met, q)
     tol = max(1e-12, 2.0 * ulp_sensitivity(cfg, met, q))
     assert tol <= 1e-5
-    errs = rel_err(dq, dqo, per_component=True)
+    errs = rhs_err(dq, cfg, met, q, per_component=True)
     assert max(errs) <= tol, (errs, tol)
+    blk.close()
+
+
+@pytest.mark.parametrize("dims,M,seed", [(2, 6, 5), (3, 6, 3), (3, 4, 3)])
+def test_wenocu6_rhs_parity_fp64_well_conditioned(dims, M, seed):
+    """WENOCU6 in FP64 at 1e-12, on smooth states whose residual is well conditioned: a 40 %
+    smooth perturbation (density and pressure stay above 0.5) keeps every sub-stencil's
+    smoothness indicator away from zero, so tau6/beta_k does not react to the last bits of
+    the data.  The oracle's own response to one-ulp input changes is checked to be below
+    5e-13 first, so the 1e-12 bound is met by agreement, not by a conditioning allowance."""
+    CU = B.FP_WENOCU6
+    Gn = O.node_ghost(M, CU)
+    if dims == 2:
+        g = I.periodic_wavy_2d(32, L=10.0, amp=0.1, Gn=Gn)
+        qinf = I.uniform_qinf(0.5, 30.0, rho=1.0, p=1.0)
+    else:
+        g = I.periodic_wavy_3d((20, 18, 16), L=10.0, amp=0.08, Gn=Gn)
+        qinf = I.uniform_qinf(0.5, 30.0, 10.0, rho=1.0, p=1.0)
+    q = I.random_smooth_state(g, qinf, amp=0.4, seed=seed)
+    cfg = O.cfg_for(g, M=M, scheme=CU, qinf=qinf)
+    met = O.metrics(cfg, g.nodes, g.Gn)
+    assert ulp_sensitivity(cfg, met, q) <= 5e-13
+    blk = Block(g, metric_order=M, scheme=CU, precision=F64, q_inf=qinf)
+    dq = blk.rhs(blk.to_device(q)).cpu().numpy()
+    errs = rhs_err(dq, cfg, met, q, per_component=True)
+    assert max(errs) <= 1e-12, errs
     blk.close()
 
 
@@ -709,12 +754,11 @@ def test_wenocu6_rhs_parity_fp64(name, M, charwise, fp):
 def test_wenocu6_rhs_parity_fp32_mixed(name, M):
     CU = B.FP_WENOCU6
     g, qinf, q = _case(name, M, CU)
-    q32 = q.astype(np.float32).astype(np.float64)
+    q32, qinf = f32(q), f32(qinf)
     blk = Block(g, metric_order=M, scheme=CU, precision=F32, q_inf=qinf)
     dq = blk.rhs(blk.to_device(q32)).cpu().numpy()
     cfg = O.cfg_for(g, M=M, scheme=CU, qinf=qinf)
-    _, dqo = O.rhs(cfg, O.metrics(cfg, g.nodes, g.Gn), q32)
-    errs = rel_err(dq, dqo, per_component=True)
+    errs = rhs_err(dq, cfg, O.metrics(cfg, g.nodes, g.Gn), q32, per_component=True)
     assert max(errs) <= 1e-5, errs
     blk.close()
 
@@ -788,20 +832,17 @@ def test_pipe_host_states_equal_the_device_batch():
 
 
 # ---- full-size parity in the benchmark's launch configuration ----
-def _full_scale(dq):
-    s = dq.abs().amax(dim=(1, 2, 3)).cpu().numpy()
-    return np.maximum(s, 1e-1 * s.max())
-
-
 def test_full_size_batched_workload_sampled_parity():
     """The 64-block batched workload at full size (34.5M points) with the benchmark's autotuned
     tiles and persistent launches (the residual call runs one launch per pass over all blocks;
     the timed graph runs the same kernel over two halves of the blocks, equal per block bit for
-    bit, see the batch tests): dQ/dt of sampled blocks against the oracle on interior sub-boxes.  FP32 on a Mach 3
-    stream with a 1e-3 perturbation: bound 3e-5 of each block's residual scale."""
+    bit, see the batch tests): dQ/dt of sampled blocks against the oracle on interior
+    sub-boxes next to the low corner, in the middle and next to the high corner.  FP32 on a
+    Mach 3 stream with a 1e-3 perturbation (float-rounded state and q_inf on both sides):
+    within 1e-5 of the parity metric."""
     M = 6
     Gn = O.node_ghost(M)
-    qinf = I.uniform_qinf(3.0, 0.0)
+    qinf = f32(I.uniform_qinf(3.0, 0.0))
     sizes = I.batched_block_sizes(64, 32, 128, 4)
     rng = np.random.default_rng(1004)
     sample = (0, 7, 19, 33, 45, 60)
@@ -809,7 +850,7 @@ def test_full_size_batched_workload_sampled_parity():
     for k, n in enumerate(sizes):
         g = (I.cylinder_ogrid(n, Lz=float(rng.uniform(1.0, 8.0)), Gn=Gn) if k < 32
              else I.periodic_wavy_3d(n, L=10.0, amp=0.08, Gn=Gn))
-        q = I.perturbed_state(g, qinf, amp=1e-3, seed=k).astype(np.float32).astype(np.float64)
+        q = f32(I.perturbed_state(g, qinf, amp=1e-3, seed=k))
         blk = Block(g, metric_order=M, precision=F32, q_inf=qinf)
         states.append(blk.to_device(q))
         blocks.append(blk)
@@ -822,12 +863,10 @@ def test_full_size_batched_workload_sampled_parity():
     for k in sample:
         g, q = keep[k]
         n = np.array(sizes[k])
-        scale = _full_scale(outs[k])
         for lo in (np.array([G, G, G]), (n - 6) // 2, n - 6 - G):
-            ref = oracle_subbox_dqdt(g, q, M, lo, np.array((6, 6, 6)), qinf=qinf)
             got = outs[k][:, lo[2]:lo[2] + 6, lo[1]:lo[1] + 6, lo[0]:lo[0] + 6].cpu().numpy()
-            err = max(np.abs(got[c] - ref[c]).max() / scale[c] for c in range(5))
-            assert err <= 3e-5, (k, lo, err)
+            err = subbox_err(got, g, q, M, lo, np.array((6, 6, 6)), qinf=qinf)
+            assert err <= 1e-5, (k, lo, err)
     bat.close()
     for b in blocks:
         b.close()
@@ -839,18 +878,16 @@ def test_full_size_cgrid_sampled_parity():
     sub-boxes next to the wall, in the wake behind the trailing edge and in the field."""
     M = 6
     g = I.cgrid_wing(n=(512, 384, 512), Gn=O.node_ghost(M))
-    qinf = I.uniform_qinf(0.84, 3.0)
+    qinf = f32(I.uniform_qinf(0.84, 3.0))
     q = I.perturbed_state(g, qinf, amp=1e-2, seed=5).astype(np.float32)
     blk = Block(g, metric_order=M, precision=F32, q_inf=qinf)
     dq = blk.rhs(blk.to_device(q))
     torch.cuda.synchronize()
-    scale = _full_scale(dq)
     q = q.astype(np.float64)
     G = O.ghost(M)
     for lo in ((256, G, 200), (g.cut - 3, 20, 100), (300, 200, 400)):
         lo = np.array(lo)
-        ref = oracle_subbox_dqdt(g, q, M, lo, np.array((6, 6, 6)), qinf=qinf)
         got = dq[:, lo[2]:lo[2] + 6, lo[1]:lo[1] + 6, lo[0]:lo[0] + 6].cpu().numpy()
-        err = max(np.abs(got[c] - ref[c]).max() / scale[c] for c in range(5))
+        err = subbox_err(got, g, q, M, lo, np.array((6, 6, 6)), qinf=qinf)
         assert err <= 1e-5, (lo, err)
     blk.close()

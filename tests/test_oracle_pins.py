@@ -103,6 +103,53 @@ def test_weno5_fifth_order_on_smooth_data_and_weights_tend_to_optimal():
     assert errs_w[2] < 10 * errs_l[2]      # WENO-JS loses some accuracy at critical points
 
 
+def _parabola_through_cell_averages(vals, cells):
+    """p(x) = a0 + a1 x + a2 x^2 whose averages over [c - 1/2, c + 1/2] are vals (h = 1)."""
+    A = np.array([[((c + 0.5) ** (j + 1) - (c - 0.5) ** (j + 1)) / (j + 1) for j in range(3)] for c in cells])
+    return np.polynomial.Polynomial(np.linalg.solve(A, vals))
+
+
+def test_weno5_smoothness_indicators_and_face_values_follow_their_definitions():
+    """Sec. 2.2.2, Eqs. weno and weno_wights: sub-stencil k covers the cells i-2+k .. i+k;
+    q_k is the value at the face i+1/2 of the parabola whose cell averages there are the
+    data, and beta_k = sum_{l=1,2} int_{cell i} h^(2l-1) (p_k^(l))^2 (Jiang & Shu's
+    definition, h = 1).  Evaluated here by an independent least-squares-free solve and
+    exact polynomial integration, so a swapped 1/4 <-> 13/12, a wrong sign inside a
+    square or a shifted sub-stencil fails."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        v = rng.standard_normal(5)
+        q, beta = O.weno5_parts(v)
+        for k in range(3):
+            cells = np.arange(k - 2, k + 1)
+            p = _parabola_through_cell_averages(v[cells + 2], cells)
+            b = 0.0
+            for l in (1, 2):
+                it = (p.deriv(l) ** 2).integ()
+                b += it(0.5) - it(-0.5)
+            assert abs(b - beta[k]) <= 1e-12 * (1 + abs(b)), (k, b, beta[k])
+            assert abs(p(0.5) - q[k]) <= 1e-13 * (1 + np.abs(v).sum()), (k, p(0.5), q[k])
+
+
+@pytest.mark.parametrize("s", [1.0, 1e-3])
+def test_weno5_weights_use_epsilon_1e6_and_power_2(s):
+    """A step in the last value, v = s (0, 0, 0, 0, 1): beta = (0, 0, 4/3 s^2) and
+    q = (0, 0, -s/6), so the WENO5-JS value is -(s/6) w_2 with
+    w_2 = [0.3/(4/3 s^2 + eps)^2] / [0.1/eps^2 + 0.6/eps^2 + 0.3/(4/3 s^2 + eps)^2].
+    With s = 1 the value is about -4e-14 and scales with eps^2; with s = 1e-3 the indicator
+    is of the size of eps and w_2 = 0.073.  Either fails for another eps or power."""
+    eps = 1e-6
+    a2 = 0.3 / (4.0 / 3.0 * s * s + eps) ** 2
+    w2 = a2 / (0.7 / eps ** 2 + a2)
+    ref = -(s / 6.0) * w2
+    got = O.weno5([0.0, 0.0, 0.0, 0.0, s])
+    assert abs(got - ref) <= 1e-12 * abs(ref), (got, ref)
+    for wrong_eps, power in ((1e-5, 2), (1e-7, 2), (1e-6, 1)):
+        a2w = 0.3 / (4.0 / 3.0 * s * s + wrong_eps) ** power
+        other = -(s / 6.0) * a2w / (0.7 / wrong_eps ** power + a2w)
+        assert abs(other - ref) > 1e-3 * abs(ref)      # the pin discriminates
+
+
 def test_weno5_is_non_oscillatory_across_a_step():
     # the upwind-biased reconstruction at i+1/2 with a jump between i and i+1 keeps the left value
     assert abs(O.weno5([0.0, 0.0, 0.0, 1.0, 1.0])) < 1e-10
