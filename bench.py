@@ -200,12 +200,13 @@ def workload_grids(I, Gn, nblocks, world, rank):
     return idx, sizes, grids
 
 
-def time_batch(torch, batch, dt, steps, warmup, stream):
+def time_batch(torch, batch, dt, steps, warmup, stream, label="timed_leg"):
     """CUDA-event time of `steps` graph replays after `warmup` (ms, total) and the sum of the
-    per-replay times (ms)."""
+    per-replay times (ms); the replays sit in an NVTX range named `label`."""
     for _ in range(warmup):
         batch.rk3_step(dt)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push(label)
     gs = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ge = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -216,6 +217,7 @@ def time_batch(torch, batch, dt, steps, warmup, stream):
         ge[s].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     return e0.elapsed_time(e1), sum(a.elapsed_time(b) for a, b in zip(gs, ge))
 
 
@@ -364,7 +366,7 @@ def run_gpu(args):
         lstates = [q.clone() for q in states]
         lbatch = Batch(lblocks, lstates, autotune=True)
         lsteps = max(10, args.steps // 2)
-        lms, lgraph = time_batch(torch, lbatch, dt, lsteps, 3, stream)
+        lms, lgraph = time_batch(torch, lbatch, dt, lsteps, 3, stream, "timed_lu5")
         lms = max_over_ranks(lms, "cuda")
         lpass = lgraph / (lsteps * passes_per_step)
         lu5 = {"workload": "the headline's batched workload with linear upwind (Eq. linear_upwind) in the FP form, "

@@ -57,7 +57,7 @@ enum { FP_WENO5_JS = 0, FP_LINEAR_UPWIND5 = 1, FP_WENO7_JS = 2, FP_WENOCU6 = 3 }
    value, C = 20, power 2, epsilon 1e-40) */
 enum { FP_F64 = 0, FP_F32_MIXED = 1 };                      /* precision of the sweep */
 enum { FP_BC_PERIODIC = 0, FP_BC_FARFIELD = 1, FP_BC_EXTRAP = 2, FP_BC_SLIP_WALL = 3, FP_BC_CUT = 4,
-       FP_BC_BLOCK = 5 };
+       FP_BC_BLOCK = 5, FP_BC_HALO = 6 };
 enum { FP_XI = 0, FP_ETA = 1, FP_ZETA = 2 };
 
 typedef struct {
@@ -86,7 +86,13 @@ typedef struct {
                                    ghost x' beyond this side is the linked block's cell next to
                                    its opposite side (x - n or n_linked + x), same transverse
                                    indices, read at the same RK stage; single-block calls
-                                   (fp_rhs, fp_rk3_step, fp_rhs_noalloc) reject such blocks */
+                                   (fp_rhs, fp_rk3_step, fp_rhs_noalloc) reject such blocks;
+                                 FP_BC_HALO      cells another process holds (a block split into
+                                   slabs across GPUs): ghost x' is read from the caller's halo
+                                   buffer of that side (fp_set_halo), which the caller refreshes
+                                   before every RK stage (fp_pack_halo on the neighbour, an
+                                   exchange, fp_rk3_stage); the ghost nodes given to
+                                   fp_init_grid there must be the neighbour's nodes */
   double gamma;               /* ratio of specific heats (Sec. 2.1 Eq. EOS: 1.4) */
   double q_inf[5];            /* far-field state; also the reference state of the FP32 form.
                                  With FP_F32_MIXED it is used as float values, like the state
@@ -130,6 +136,28 @@ int fp_rhs(fp_ctx *ctx, const void *q_dev, void *dqdt_dev, void *stream);
    whose updated state is not finite sets a device flag that fp_get_device_status()
    reports. */
 int fp_rk3_step(fp_ctx *ctx, void *q_dev, double dt, void *stream);
+
+/* One of the three stages of fp_rk3_step (stage 0, 1, 2 in order, the same dt; stage 0 reads
+   q_dev, stage 2 writes the step's result into q_dev).  For blocks with FP_BC_HALO sides,
+   whose halos must hold the neighbours' cells of the same stage before each stage runs
+   (Sec. 2.2 third-order TVD Runge-Kutta, split at its stages).  fp_rk3_step rejects such
+   blocks; any block may be advanced this way. */
+int fp_rk3_stage(fp_ctx *ctx, void *q_dev, double dt, int stage, void *stream);
+
+/* Halo of an FP_BC_HALO side (dir, side): halo_dev is a caller-owned device buffer of
+   fp_halo_bytes(ctx, dir) bytes holding the G = fp_ghost_width cells beyond that side, laid
+   out like the state with the extent n_dir replaced by G; its index along dir follows the grid
+   index (cells -G..-1 below the low side, or n..n+G-1 above the high side, are halo indices
+   0..G-1).  Kept by the context and read by every later pass until replaced.  FP_ERR_ARG if
+   that side is not FP_BC_HALO. */
+int fp_set_halo(fp_ctx *ctx, int dir, int side, void *halo_dev);
+size_t fp_halo_bytes(const fp_ctx *ctx, int dir);
+
+/* The G cells next to side (dir, side) of stage state `stage` (0: q_dev, 1 and 2: the
+   context's stage buffers, as left by fp_rk3_stage of the previous stage), written to out_dev
+   in the layout of the halo the neighbour across that side reads (low side: cells 0..G-1,
+   high side: cells n-G..n-1).  Stream-ordered; allocates nothing. */
+int fp_pack_halo(fp_ctx *ctx, const void *q_dev, int stage, int dir, int side, void *out_dev, void *stream);
 
 /* dt = cfl / max over points of sum_d (|U_d| + c |grad d|), grad d = J (d_x, d_y, d_z)/J.
    Synchronises `stream` to return the value in *dt_out (host). */

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libfpgb300.so")
 FP_OK, FP_ERR_ARG, FP_ERR_CUDA, FP_ERR_OOM, FP_ERR_NONFINITE, FP_ERR_TIMEOUT, FP_ERR_UNSUPPORTED = range(7)
 FP_WENO5_JS, FP_LINEAR_UPWIND5, FP_WENO7_JS, FP_WENOCU6 = 0, 1, 2, 3
 FP_F64, FP_F32_MIXED = 0, 1
-FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP, FP_BC_SLIP_WALL, FP_BC_CUT, FP_BC_BLOCK = 0, 1, 2, 3, 4, 5
+FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP, FP_BC_SLIP_WALL, FP_BC_CUT, FP_BC_BLOCK, FP_BC_HALO = 0, 1, 2, 3, 4, 5, 6
 
 # every symbol include/fp.h declares
 EXPORTS = [
@@ -26,7 +26,8 @@ EXPORTS = [
     "fp_free", "fp_batch_create", "fp_batch_create_linked", "fp_batch_rk3_step", "fp_batch_rhs", "fp_batch_launches_per_step",
     "fp_batch_last_error", "fp_batch_free", "fp_state_bytes", "fp_pipe_create", "fp_pipe_rk3_step_host",
     "fp_pipe_groups", "fp_pipe_launches_per_step", "fp_pipe_last_error", "fp_pipe_free",
-    "fp_balanced_groups", "fp_debug_fail_allocation", "fp_probe_peaks",
+    "fp_balanced_groups", "fp_debug_fail_allocation", "fp_probe_peaks", "fp_rk3_stage", "fp_set_halo",
+    "fp_halo_bytes", "fp_pack_halo",
 ]
 
 
@@ -100,6 +101,11 @@ def lib():
                                          ctypes.POINTER(ctypes.c_int)]
         L.fp_debug_fail_allocation.argtypes = [ctypes.c_int]
         L.fp_probe_peaks.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3 + [_VP]
+        L.fp_rk3_stage.argtypes = [_VP, _VP, ctypes.c_double, ctypes.c_int, _VP]
+        L.fp_set_halo.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
+        L.fp_halo_bytes.argtypes = [_VP, ctypes.c_int]
+        L.fp_halo_bytes.restype = ctypes.c_size_t
+        L.fp_pack_halo.argtypes = [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP]
         _lib = L
     return _lib
 
@@ -169,6 +175,22 @@ def fp_rhs_noalloc(ctx, q_ptr, dqdt_ptr, stream=0):
 
 def fp_rk3_step(ctx, q_ptr, dt, stream=0):
     _check(lib().fp_rk3_step(ctx, q_ptr, float(dt), stream), ctx)
+
+
+def fp_rk3_stage(ctx, q_ptr, dt, stage, stream=0):
+    _check(lib().fp_rk3_stage(ctx, q_ptr, float(dt), int(stage), stream), ctx)
+
+
+def fp_set_halo(ctx, direction, side, halo_ptr):
+    _check(lib().fp_set_halo(ctx, int(direction), int(side), halo_ptr), ctx)
+
+
+def fp_halo_bytes(ctx, direction):
+    return lib().fp_halo_bytes(ctx, int(direction))
+
+
+def fp_pack_halo(ctx, q_ptr, stage, direction, side, out_ptr, stream=0):
+    _check(lib().fp_pack_halo(ctx, q_ptr, int(stage), int(direction), int(side), out_ptr, stream), ctx)
 
 
 def fp_cfl_dt(ctx, q_ptr, cfl, stream=0):

@@ -180,6 +180,14 @@ int has_link(const fp_grid_desc &d) {
   return 0;
 }
 
+// some side of the block takes its ghosts from a caller's halo buffer
+int has_halo(const fp_grid_desc &d) {
+  for (int k = 0; k < d.dims; ++k)
+    for (int s = 0; s < 2; ++s)
+      if (d.bc[k][s] == FP_BC_HALO) return 1;
+  return 0;
+}
+
 int ghost_of(int M, int scheme) { return std::max(scheme == FP_WENO7_JS ? 4 : 3, M / 2); }
 
 int prepare(int is_f32, int M, int scheme) {
@@ -236,6 +244,19 @@ void fill_dirs(fp_ctx *c) {
     D.bchi = c->desc.bc[d][1];
     D.fmet = c->fmet[d];
     D.dk = c->dk[d];
+    D.halo[0] = D.halo[1] = nullptr;
+    // halo layout: the state layout with this direction's extent replaced by G
+    {
+      long long e[3] = {ni, nj, nk};
+      e[d] = G;
+      const long long s1 = e[0], s2 = e[0] * e[1];
+      const long long st[3] = {1, s1, s2};
+      const int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2;   // the line's t1 and t2 directions
+      D.hsd = st[d];
+      D.hT1 = st[ta];
+      D.hT2 = st[tb];
+      D.hc = e[0] * e[1] * e[2];
+    }
     if (d < dims) default_tile(d, D.nd, &D.S, &D.TT);
     else { D.S = 8; D.TT = 32; D.nlines = 0; }
   }
@@ -313,7 +334,8 @@ int validate(const fp_grid_desc *d, int ghost_nodes, std::string &why) {
   if (d->global_lf != 0 && d->global_lf != 1) { why = "global_lf must be 0 or 1"; return 0; }
   for (int k = 0; k < d->dims; ++k)
     for (int s = 0; s < 2; ++s)
-      if (d->bc[k][s] < 0 || d->bc[k][s] > FP_BC_BLOCK) { why = "unknown boundary code"; return 0; }
+      if (d->bc[k][s] < 0 || d->bc[k][s] > FP_BC_HALO) { why = "unknown boundary code"; return 0; }
+  if (d->global_lf && has_halo(*d)) { why = "global_lf with FP_BC_HALO sides (the speeds would be per block)"; return 0; }
   if (d->cut_width < 0) { why = "cut_width must be non-negative"; return 0; }
   if (!(d->gamma > 1.0) || !std::isfinite(d->gamma)) { why = "gamma must exceed 1"; return 0; }
   const double rho = d->q_inf[0];
@@ -471,30 +493,47 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
   return FP_OK;
 }
 
-static int run_passes(fp_ctx *c, int rk, cudaStream_t s) {
+// the direction passes of one RK stage (rk = 1: the last pass applies the stage update) or
+// of one residual (rk = 0)
+static int run_stage(fp_ctx *c, int stage, int rk, cudaStream_t s) {
   const int dims = c->desc.dims, M = c->desc.metric_order;
-  for (int stage = 0; stage < (rk ? 3 : 1); ++stage) {
-    if (c->desc.global_lf) {
-      cudaError_t e = fpk::launch_lambda(c->dblk, 1, c->lam_items, c->nlam_items, c->is_f32,
-                                         c->desc.characteristic, stage, s);
-      if (e != cudaSuccess) return cuda_fail(c, e, "global speed launch");
-    }
-    for (int d = 0; d < dims; ++d) {
-      fpk::SweepLaunch L;
-      L.blocks = c->dblk;
-      L.items = c->items[d];
-      L.nitems = c->nitems[d];
-      L.dir = d;
-      L.mode = d == 0 ? fpk::MODE_WRITE : (d == dims - 1 ? (rk ? fpk::MODE_RK : fpk::MODE_RHS) : fpk::MODE_ADD);
-      L.stage = stage;
-      L.dt = c->dt_dev;
-      L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
-      L.bnd = has_bnd(c->desc, d);
-      cudaError_t e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic,
-                             c->desc.free_stream_preserving, s);
-      if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
-    }
+  if (c->desc.global_lf) {
+    cudaError_t e = fpk::launch_lambda(c->dblk, 1, c->lam_items, c->nlam_items, c->is_f32,
+                                       c->desc.characteristic, stage, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "global speed launch");
   }
+  for (int d = 0; d < dims; ++d) {
+    fpk::SweepLaunch L;
+    L.blocks = c->dblk;
+    L.items = c->items[d];
+    L.nitems = c->nitems[d];
+    L.dir = d;
+    L.mode = d == 0 ? fpk::MODE_WRITE : (d == dims - 1 ? (rk ? fpk::MODE_RK : fpk::MODE_RHS) : fpk::MODE_ADD);
+    L.stage = stage;
+    L.dt = c->dt_dev;
+    L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
+    L.bnd = has_bnd(c->desc, d);
+    cudaError_t e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic,
+                           c->desc.free_stream_preserving, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
+  }
+  return FP_OK;
+}
+
+static int run_passes(fp_ctx *c, int rk, cudaStream_t s) {
+  for (int stage = 0; stage < (rk ? 3 : 1); ++stage) {
+    int st = run_stage(c, stage, rk, s);
+    if (st) return st;
+  }
+  return FP_OK;
+}
+
+// every FP_BC_HALO side has its buffer
+static int halos_set(fp_ctx *c, const char *who) {
+  for (int d = 0; d < c->desc.dims; ++d)
+    for (int sd = 0; sd < 2; ++sd)
+      if (c->desc.bc[d][sd] == FP_BC_HALO && !c->hblk.dir[d].halo[sd])
+        return fail(c, FP_ERR_ARG, std::string(who) + ": an FP_BC_HALO side has no halo buffer (fp_set_halo)");
   return FP_OK;
 }
 
@@ -502,6 +541,7 @@ int fp_rhs(fp_ctx *c, const void *q, void *dqdt, void *stream) {
   if (!c) return FP_ERR_ARG;
   if (!q || !dqdt) return fail(c, FP_ERR_ARG, "fp_rhs: null buffer");
   if (has_link(c->desc)) return fail(c, FP_ERR_ARG, "fp_rhs: FP_BC_BLOCK sides need a linked batch");
+  if (int st = halos_set(c, "fp_rhs")) return st;
   cudaStream_t s = (cudaStream_t)stream;
   c->hblk.q[0] = const_cast<void *>(q);
   c->hblk.dqdt = dqdt;
@@ -515,6 +555,8 @@ int fp_rk3_step(fp_ctx *c, void *q, double dt, void *stream) {
   if (!q) return fail(c, FP_ERR_ARG, "fp_rk3_step: null state");
   if (!std::isfinite(dt)) return fail(c, FP_ERR_ARG, "fp_rk3_step: dt not finite");
   if (has_link(c->desc)) return fail(c, FP_ERR_ARG, "fp_rk3_step: FP_BC_BLOCK sides need a linked batch");
+  if (has_halo(c->desc))
+    return fail(c, FP_ERR_ARG, "fp_rk3_step: FP_BC_HALO sides need their halos refreshed between stages (fp_rk3_stage)");
   cudaStream_t s = (cudaStream_t)stream;
   c->hblk.q[0] = q;
   int st = sync_block(c, s);
@@ -523,6 +565,48 @@ int fp_rk3_step(fp_ctx *c, void *q, double dt, void *stream) {
   cudaError_t e = cudaMemcpyAsync(c->dt_dev, &c->dt_host, sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "upload dt");
   return run_passes(c, 1, s);
+}
+
+int fp_rk3_stage(fp_ctx *c, void *q, double dt, int stage, void *stream) {
+  if (!c) return FP_ERR_ARG;
+  if (!q) return fail(c, FP_ERR_ARG, "fp_rk3_stage: null state");
+  if (stage < 0 || stage > 2) return fail(c, FP_ERR_ARG, "fp_rk3_stage: stage must be 0, 1 or 2");
+  if (!std::isfinite(dt)) return fail(c, FP_ERR_ARG, "fp_rk3_stage: dt not finite");
+  if (has_link(c->desc)) return fail(c, FP_ERR_ARG, "fp_rk3_stage: FP_BC_BLOCK sides need a linked batch");
+  if (int st = halos_set(c, "fp_rk3_stage")) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->hblk.q[0] = q;
+  int st = sync_block(c, s);
+  if (st) return st;
+  if (stage == 0) {   // one dt for the three stages of a step
+    c->dt_host = dt;
+    cudaError_t e = cudaMemcpyAsync(c->dt_dev, &c->dt_host, sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload dt");
+  }
+  return run_stage(c, stage, 1, s);
+}
+
+int fp_set_halo(fp_ctx *c, int dir, int side, void *halo_dev) {
+  if (!c) return FP_ERR_ARG;
+  if (dir < 0 || dir >= c->desc.dims || side < 0 || side > 1 || !halo_dev)
+    return fail(c, FP_ERR_ARG, "fp_set_halo: bad direction, side or buffer");
+  if (c->desc.bc[dir][side] != FP_BC_HALO) return fail(c, FP_ERR_ARG, "fp_set_halo: that side is not FP_BC_HALO");
+  c->hblk.dir[dir].halo[side] = halo_dev;
+  return FP_OK;
+}
+
+size_t fp_halo_bytes(const fp_ctx *c, int dir) {
+  if (!c || dir < 0 || dir >= c->desc.dims) return 0;
+  return (size_t)5 * (size_t)(c->ncells / c->desc.n[dir]) * (size_t)c->G * c->esize;
+}
+
+int fp_pack_halo(fp_ctx *c, const void *q, int stage, int dir, int side, void *out_dev, void *stream) {
+  if (!c) return FP_ERR_ARG;
+  if (!q || !out_dev || stage < 0 || stage > 2 || dir < 0 || dir >= c->desc.dims || side < 0 || side > 1)
+    return fail(c, FP_ERR_ARG, "fp_pack_halo: bad argument");
+  const void *src = stage == 0 ? q : (stage == 1 ? c->q1 : c->q2);
+  cudaError_t e = fpk::launch_pack_halo(src, c->is_f32, dir, side, c->G, c->desc.n, out_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? FP_OK : cuda_fail(c, e, "fp_pack_halo");
 }
 
 int fp_cfl_dt(fp_ctx *c, const void *q, double cfl, double *dt_out, void *stream) {
@@ -756,7 +840,7 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
   *out = nullptr;
   if (!blocks || !q_devs || nblocks < 1 || nlinks < 0 || (nlinks > 0 && !links)) return FP_ERR_ARG;
   for (int k = 0; k < nblocks; ++k)
-    if (!blocks[k] || !q_devs[k]) return FP_ERR_ARG;
+    if (!blocks[k] || !q_devs[k] || has_halo(blocks[k]->desc)) return FP_ERR_ARG;
   // every FP_BC_BLOCK side linked exactly once, to a block with the same transverse extents
   std::vector<int> nbr((size_t)nblocks * 6, -1);
   for (int l = 0; l < nlinks; ++l) {
@@ -942,6 +1026,7 @@ extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream
   if (!c) return FP_ERR_ARG;
   if (!q || !dqdt) return fail(c, FP_ERR_ARG, "fp_rhs_noalloc: null buffer");
   if (has_link(c->desc)) return fail(c, FP_ERR_ARG, "fp_rhs_noalloc: FP_BC_BLOCK sides need a linked batch");
+  if (int st = halos_set(c, "fp_rhs_noalloc")) return st;
   const size_t need = (size_t)5 * (size_t)c->ncells * c->esize;
   if (need > kNoAllocScratchBytes) {
     char msg[256];

@@ -1,5 +1,6 @@
 // cfl.cu - time-step bound: max over points of sum_d (|u . grad d| + c |grad d|),
-// grad d = J (d_x, d_y, d_z)/J, reduced to one value per launch.
+// grad d = J (d_x, d_y, d_z)/J, reduced to one value per launch; the global Lax-Friedrichs
+// speeds; and the packing of the cells a neighbouring process needs as its halo.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -115,7 +116,48 @@ __global__ void k_lam_max(const BlockDev *blocks, const int2 *items, int nitems,
   }
 }
 
+// The G cells next to one side of a block, in the halo layout the receiving block reads:
+// the state layout [5][nk][nj][ni] with the extent of direction `dir` replaced by G.  Low
+// side: cells 0..G-1; high side: cells n-G..n-1 (index x - (n - G) in the buffer).
+template <typename T>
+__global__ void k_pack_halo(const T *__restrict__ q, T *__restrict__ out, int dir, int side, int G, int ni,
+                            int nj, int nk) {
+  int e[3] = {ni, nj, nk};
+  const int nd = e[dir];
+  e[dir] = G;
+  const long long hc = (long long)e[0] * e[1] * e[2], qc = (long long)ni * nj * nk;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < 5 * hc;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(idx / hc);
+    long long r = idx - v * hc;
+    int c[3];
+    c[0] = (int)(r % e[0]);
+    r /= e[0];
+    c[1] = (int)(r % e[1]);
+    c[2] = (int)(r / e[1]);
+    c[dir] += side ? nd - G : 0;
+    out[idx] = q[v * qc + ((long long)c[2] * nj + c[1]) * ni + c[0]];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pack_halo(const void *q, int is_f32, int dir, int side, int G, const int *n, void *out,
+                             cudaStream_t s) {
+  int e[3] = {n[0], n[1], n[2]};
+  e[dir] = G;
+  const long long total = 5LL * e[0] * e[1] * e[2];
+  const int threads = 256;
+  const long long want = (total + threads - 1) / threads;
+  const int grid = (int)(want < 4096 ? (want < 1 ? 1 : want) : 4096);
+  if (is_f32)
+    k_pack_halo<float><<<grid, threads, 0, s>>>(static_cast<const float *>(q), static_cast<float *>(out), dir, side, G,
+                                                n[0], n[1], n[2]);
+  else
+    k_pack_halo<double><<<grid, threads, 0, s>>>(static_cast<const double *>(q), static_cast<double *>(out), dir, side,
+                                                 G, n[0], n[1], n[2]);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_lambda(const BlockDev *blocks, int nblocks, const int2 *items, int nitems, int is_f32,
                           int charwise, int stage, cudaStream_t s) {

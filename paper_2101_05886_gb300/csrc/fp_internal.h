@@ -43,6 +43,10 @@ struct DirDev {
   int S, TT;           // faces per chunk, lines per tile (S * TT == kThreads)
   const void *fmet;    // T [3][faces]
   const void *dk;      // T [3][cells]: k_{i+1/2} - k_{i-1/2} along this direction (FP64-formed)
+  // FP_BC_HALO sides: the caller's buffers of the G cells beyond each side, laid out like the
+  // state with this direction's extent replaced by G (strides: t1, t2, along the line, component)
+  const void *halo[2];
+  long long hT1, hT2, hsd, hc;
 };
 
 // 16-byte aligned and padded so that the sweep can copy a descriptor into shared memory in
@@ -127,5 +131,10 @@ cudaError_t launch_lambda(const BlockDev *blocks, int nblocks, const int2 *items
 // CFL reduction (cfl.cu).
 cudaError_t launch_cfl(const BlockDev *blk, int is_f32, long long ncells, const int *n, int dims,
                        unsigned long long *out_bits, cudaStream_t s);
+
+// Halo packing (cfl.cu): the G cells of stage state `stage` next to side `side` of direction
+// `dir` into `out`, in the halo layout of DirDev (the receiving block's view of them).
+cudaError_t launch_pack_halo(const void *q, int is_f32, int dir, int side, int G, const int *n, void *out,
+                             cudaStream_t s);
 
 }  // namespace fpk

@@ -437,7 +437,8 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     // momentum to be reflected about the boundary face's normal.  Codes: 0 periodic, 1 far
     // field, 2 zero gradient, 3 slip wall (mirror cell), 4 C-grid cut (mirror cell on the line
     // with t1 reversed, wall outside the cut width), 5 another block of the batch (its cells
-    // next to its opposite side, same transverse indices, same RK stage).
+    // next to its opposite side, same transverse indices, same RK stage), 6 the caller's halo
+    // buffer of that side (the cells another process holds, refreshed for every RK stage).
     auto bc_source = [&](int x, const T *&src, long long &cs, bool &far, bool &wall) {
       int xx = x;
       long long qsrc = qbase;
@@ -447,7 +448,12 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         if (bc == 0) { xx = x % nd; if (xx < 0) xx += nd; }
         else if (bc == 1) far = true;
         else if (bc == 2 || !BND) xx = x < 0 ? 0 : nd - 1;
-        else if (bc == 5) {   // rare path: the line's (t1, t2) are recovered from its offset
+        else if (bc == 6) {   // halo buffer: index x + G below the line, x - nd above it
+          const long long hx = x < 0 ? (long long)(x + G) : (long long)(x - nd);
+          src = static_cast<const T *>(D->halo[x < 0 ? 0 : 1]) + t1 * D->hT1 + t2 * D->hT2 + hx * D->hsd;
+          cs = D->hc;
+          return;
+        } else if (bc == 5) {   // rare path: the line's (t1, t2) are recovered from its offset
           const BlockDev *NB = blocks + B->nbr[dir][x < 0 ? 0 : 1];
           const DirDev *ND = &NB->dir[dir];
           const long long s2 = qbase / D->qT2, s1 = (qbase - s2 * D->qT2) / D->qT1;

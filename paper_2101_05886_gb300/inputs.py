@@ -33,6 +33,7 @@ BC_EXTRAP = 2
 BC_SLIP_WALL = 3
 BC_CUT = 4
 BC_BLOCK = 5
+BC_HALO = 6
 
 
 def ghost_width(metric_order: int, scheme: int = 0) -> int:
@@ -521,12 +522,13 @@ def random_smooth_state(grid: Grid, qinf, amp=0.05, seed=0):
 # --------------------------------------------------------------------------
 # Multi-block splits
 # --------------------------------------------------------------------------
-def split_grid(grid: Grid, direction: int, sizes):
+def split_grid(grid: Grid, direction: int, sizes, side_bc: int = BC_BLOCK):
     """Split a block into consecutive blocks of the given extents along `direction`.
 
     Returns (blocks, links): each block's ghost nodes are the neighbouring blocks' nodes
     (sliced from the parent, whose own ghosts serve the outer sides); the inner sides get
-    BC_BLOCK and a link (a, direction, side, b); a periodic parent's outer sides are
+    `side_bc` (BC_BLOCK for blocks of one batch, BC_HALO for slabs held by different
+    processes) and a link (a, direction, side, b); a periodic parent's outer sides are
     linked around (last block's high side to the first block's low side).  States are
     split with `split_state`."""
     assert sum(sizes) == grid.n[direction] and min(sizes) >= 1
@@ -544,10 +546,10 @@ def split_grid(grid: Grid, direction: int, sizes):
         n[direction] = int(nloc)
         bc = [list(p) for p in grid.bc]
         if b > 0 or periodic:
-            bc[direction][0] = BC_BLOCK
+            bc[direction][0] = side_bc
             links.append((b, direction, 0, (b - 1) % nb))
         if b < nb - 1 or periodic:
-            bc[direction][1] = BC_BLOCK
+            bc[direction][1] = side_bc
             links.append((b, direction, 1, (b + 1) % nb))
         blocks.append(Grid(grid.dims, tuple(n), Gn, nodes, tuple(map(tuple, bc)),
                            f"{grid.name}_part{b}", grid.cut))

@@ -61,8 +61,11 @@ def test_other_invalid_arguments(lib):
     assert lib.fp_init_grid(ctypes.byref(d), nodes.ctypes.data, 11, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
     d2 = B.make_desc(3, (2, 8, 8), metric_order=6)
     assert lib.fp_init_grid(ctypes.byref(d2), nodes.ctypes.data, 12, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
-    d3 = B.make_desc(3, (8, 8, 8), metric_order=6, bc=((0, 6), (0, 0), (0, 0)))
+    d3 = B.make_desc(3, (8, 8, 8), metric_order=6, bc=((0, 7), (0, 0), (0, 0)))
     assert lib.fp_init_grid(ctypes.byref(d3), nodes.ctypes.data, 12, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
+    # global Lax-Friedrichs speeds would be per slab on a block with halo sides
+    d6 = B.make_desc(3, (8, 8, 8), metric_order=6, bc=((0, 0), (0, 0), (B.FP_BC_HALO, B.FP_BC_HALO)), global_lf=1)
+    assert lib.fp_init_grid(ctypes.byref(d6), nodes.ctypes.data, 12, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
     d4 = B.make_desc(2, (8, 8, 3), metric_order=2)
     assert lib.fp_init_grid(ctypes.byref(d4), nodes.ctypes.data, 6, None, ctypes.byref(ctx)) == B.FP_ERR_ARG
     d5 = B.make_desc(3, (8, 8, 8), metric_order=6, q_inf=(1.0, 0, 0, 0, -1.0))
