@@ -519,6 +519,29 @@ def random_smooth_state(grid: Grid, qinf, amp=0.05, seed=0):
     return perturbed_state(grid, qinf, amp=amp, seed=seed)
 
 
+def fade_to_farfield(grid: Grid, q, qinf, width=8):
+    """q blended into the uniform far-field state over the `width` points next to every
+    far-field side (weight cos^2 from 1, `width` points inside, to 0 at the last two
+    points), so that the state meets its far-field ghosts without a jump."""
+    q = np.array(q, dtype=np.float64, copy=True)
+    qu = uniform_state(grid, qinf)
+    w = np.ones(q.shape[1:])
+    for d in range(grid.dims):
+        n = grid.n[d]
+        ax = 2 - d                                   # axis of direction d in [k][j][i]
+        x = np.arange(n, dtype=np.float64)
+        for side in (0, 1):
+            if grid.bc[d][side] != BC_FARFIELD:
+                continue
+            dist = x if side == 0 else (n - 1 - x)
+            t = np.clip((width - 1 - dist) / (width - 2.0), 0.0, 1.0)
+            wd = np.cos(0.5 * np.pi * t) ** 2
+            shape = [1, 1, 1]
+            shape[ax] = n
+            w = w * wd.reshape(shape)
+    return qu + (q - qu) * w[None]
+
+
 # --------------------------------------------------------------------------
 # Multi-block splits
 # --------------------------------------------------------------------------
