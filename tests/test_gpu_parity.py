@@ -111,10 +111,11 @@ def _fp64_tol(cfg, met, q):
     three directions' pressure terms (about 2 % of each), and the oracle's per-field
     Lax-Friedrichs split cancels too, so the oracle itself moves by up to 1.6e-12 of this
     metric under one-ulp input changes there; a linear-upwind evaluation that projects after
-    reconstructing (no such cancellation) differs from it by about that much.  The bound
-    never exceeds 5e-12."""
+    reconstructing (no such cancellation) differs from it by about that much.  On the C-grid
+    wing, whose wall cells are 1e-7 of the far-field cells' volume, the oracle moves by up to
+    7.4e-12.  The bound never exceeds 2e-11."""
     tol = max(1e-12, 2.0 * ulp_sensitivity(cfg, met, q))
-    assert tol <= 5e-12, tol
+    assert tol <= 2e-11, tol
     return tol
 
 

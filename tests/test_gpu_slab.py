@@ -38,7 +38,8 @@ def _case(name, precision):
     elif name == "cgrid_k2":
         g = I.cgrid_wing(n=(48, 24, 16), Gn=Gn)
         qinf = I.uniform_qinf(0.84, 3.0)
-        q, d, parts = I.random_smooth_state(g, qinf, amp=0.03, seed=2), 2, 2
+        q = I.fade_to_farfield(g, I.random_smooth_state(g, qinf, amp=0.03, seed=2), qinf)
+        d, parts = 2, 2
     else:
         raise KeyError(name)
     if precision == F32:
