@@ -904,3 +904,39 @@ def test_full_size_cgrid_sampled_parity():
         err = subbox_err(got, g, q, M, lo, np.array((6, 6, 6)), qinf=qinf)
         assert err <= 1e-5, (lo, err)
     blk.close()
+
+
+# ---- the two-lines-per-thread FP32 sweep against the one-line sweep and the oracle ----
+@pytest.mark.parametrize("name,M,scheme,charwise", [("3d_vortex", 6, 0, 1), ("3d_vortex", 6, 1, 1), ("3d_ogrid", 4, 0, 1),
+                                                    ("3d_ogrid", 8, 1, 0), ("2d_vortex", 6, 0, 1), ("3d_min", 6, 1, 1)])
+def test_two_line_sweep_equals_the_one_line_sweep(name, M, scheme, charwise):
+    """FP32 WENO5-JS and linear upwind run by default with two grid lines per thread (every
+    face operation packed across the two lines); the same blocks with one line per thread
+    (fp_set_tile with faces x lines = 256) evaluate the same algebra in another operation
+    grouping: they agree within rounding, and both are within 1e-5 of the oracle.  The cases
+    include odd line counts (a thread whose second line is missing)."""
+    g, qinf, q = _case(name, M)
+    q, qinf = f32(q), f32(qinf)
+    two = Block(g, metric_order=M, scheme=scheme, characteristic=charwise, precision=F32, q_inf=qinf)
+    one = Block(g, metric_order=M, scheme=scheme, characteristic=charwise, precision=F32, q_inf=qinf)
+    for d in range(g.dims):
+        faces, lines = B.fp_get_tile(two.ctx, d)
+        assert faces * lines == 512                     # two lines per thread by default
+        B.fp_set_tile(one.ctx, d, faces, 256 // faces)
+        assert B.fp_get_tile(one.ctx, d) == (faces, 256 // faces)
+    qd = two.to_device(q)
+    d2, d1 = two.rhs(qd).cpu().numpy(), one.rhs(qd).cpu().numpy()
+    cfg = O.cfg_for(g, M=M, scheme=scheme, charwise=charwise, qinf=qinf)
+    P = Parity(cfg, O.metrics(cfg, g.nodes, g.Gn), q)
+    assert residual_err(-d2 * P.invJ, -d1 * P.invJ, P.tau) <= 2e-6
+    assert P.err(d2) <= 1e-5 and P.err(d1) <= 1e-5
+    q2, q1 = two.to_device(q), one.to_device(q)
+    dt = 0.5 * two.cfl_dt(q2, 0.5)
+    for _ in range(2):
+        two.rk3_step(q2, dt)
+        one.rk3_step(q1, dt)
+    torch.cuda.synchronize()
+    assert state_err(q2.cpu().numpy() - q, q1.cpu().numpy() - q) <= 1e-5
+    assert two.status() == B.FP_OK and one.status() == B.FP_OK
+    two.close()
+    one.close()
