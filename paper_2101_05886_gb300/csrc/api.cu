@@ -735,6 +735,10 @@ void fp_batch_free(fp_batch *b) {
 
 const char *fp_batch_last_error(const fp_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
+int fp_batch_lines_per_thread(const fp_batch *b, int dir) {
+  return (b && dir >= 0 && dir < 3) ? b->lpt[dir] : 0;
+}
+
 int fp_batch_launches_per_step(const fp_batch *b) {
   return b ? b->nbranch * 3 * (b->dims + (b->global_lf ? 2 : 0)) : 0;
 }
