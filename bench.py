@@ -243,14 +243,6 @@ def roofline(kind, ncells, pass_ms, launches_per_pass, fp32_peak, peak_src, full
                     "peak_source": hsrc, "algorithmic_bytes_per_point_stage": round(BYTES_PER_CELL_STAGE_F32, 1)}}
 
 
-def kernel_name(lpt, scheme, what):
-    """The sweep kernel a batch ran: two lines per thread (fp_sweep2) in every direction, or
-    one line per thread (fp_sweep)."""
-    if all(v == 2 for v in lpt):
-        return f"fpk::fp_sweep2<6,{scheme}> ({what}, two grid lines per thread)"
-    return f"fpk::fp_sweep<float,6,{scheme},false> ({what}; lines per thread by direction {lpt})"
-
-
 def run_gpu(args):
     import torch
     from paper_2101_05886_gb300 import binding as B
@@ -349,7 +341,7 @@ def run_gpu(args):
     pass_ms = graph_ms / (args.steps * passes_per_step)
     full = args.blocks == 64 and world == 1
     roof = roofline("weno5_char", ncells, pass_ms, launches_per_pass, fp32_peak, peak_src, full)
-    roof["kernel"] = kernel_name(batch.lines_per_thread(), 0, "characteristic WENO5-JS")
+    roof["kernel"] = "fpk::fp_sweep<float,6,0,false> (characteristic WENO5-JS)"
 
     # ---- the FP32 residual's error against the FP64 sweep (itself within 1e-12 of the FP64
     # oracle in the parity tests), on the rank's first block at its current state
@@ -386,7 +378,7 @@ def run_gpu(args):
                "roofline": roofline("lu5_char", ncells, lpass, lbatch.launches_per_step() // passes_per_step,
                                     fp32_peak, peak_src, full),
                "finite": all(b.status() == B.FP_OK for b in lblocks)}
-        lu5["roofline"]["kernel"] = kernel_name(lbatch.lines_per_thread(), 1, "characteristic linear upwind")
+        lu5["roofline"]["kernel"] = "fpk::fp_sweep<float,6,1,false> (characteristic linear upwind)"
         if rank == 0:
             lu5["fp32_error_vs_fp64"] = {"max_rel": fp32_error(lblocks[0], grids[0], lstates[0],
                                                                scheme=B.FP_LINEAR_UPWIND5), "bound": 1e-5}

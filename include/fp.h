@@ -218,12 +218,9 @@ size_t fp_state_bytes(const fp_ctx *ctx);
 int fp_launches_per_rhs(const fp_ctx *ctx);
 int fp_launches_per_step(const fp_ctx *ctx);
 
-/* Tile shape used for direction dir: faces per chunk and lines per tile; faces x lines is 256
-   (one line per thread) or 512 (two lines per thread, the default of the FP32 WENO5-JS and
-   linear-upwind sweeps in directions without slip-wall, cut, link or halo sides). */
+/* Tile shape used for direction dir: faces per chunk and lines per tile. */
 int fp_get_tile(const fp_ctx *ctx, int dir, int *faces, int *lines);
-/* Override the tile shape: faces in {8,16,32}, faces x lines == 256 for one line per thread or
-   512 for two (only where the two-line sweep serves the direction, else FP_ERR_ARG). */
+/* Override the tile shape (faces in {8,16,32}, faces*lines == 256). */
 int fp_set_tile(fp_ctx *ctx, int dir, int faces, int lines);
 
 const char *fp_last_error(const fp_ctx *ctx);
@@ -266,11 +263,6 @@ int fp_batch_rk3_step(fp_batch *batch, double dt, void *stream);
 /* dqdt for every block (no graph); dqdt_devs[b] has block b's state layout. */
 int fp_batch_rhs(fp_batch *batch, void *const *dqdt_devs, void *stream);
 int fp_batch_launches_per_step(const fp_batch *batch);
-/* Grid lines per thread of the batch's sweep in direction dir: 2 when every block runs the
-   FP32 WENO5-JS or linear-upwind sweep without slip-wall, cut, link or halo sides there (each
-   thread then carries two lines, every face operation packed across them), else 1; 0 for a
-   NULL batch or a bad direction. */
-int fp_batch_lines_per_thread(const fp_batch *batch, int dir);
 const char *fp_batch_last_error(const fp_batch *batch);
 void fp_batch_free(fp_batch *batch);       /* NULL-safe */
 

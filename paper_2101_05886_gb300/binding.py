@@ -27,7 +27,7 @@ EXPORTS = [
     "fp_batch_last_error", "fp_batch_free", "fp_state_bytes", "fp_pipe_create", "fp_pipe_rk3_step_host",
     "fp_pipe_groups", "fp_pipe_launches_per_step", "fp_pipe_last_error", "fp_pipe_free",
     "fp_balanced_groups", "fp_debug_fail_allocation", "fp_probe_peaks", "fp_rk3_stage", "fp_set_halo",
-    "fp_halo_bytes", "fp_pack_halo", "fp_batch_lines_per_thread",
+    "fp_halo_bytes", "fp_pack_halo",
 ]
 
 
@@ -82,7 +82,6 @@ def lib():
         L.fp_batch_rk3_step.argtypes = [_VP, ctypes.c_double, _VP]
         L.fp_batch_rhs.argtypes = [_VP, ctypes.POINTER(_VP), _VP]
         L.fp_batch_launches_per_step.argtypes = [_VP]
-        L.fp_batch_lines_per_thread.argtypes = [_VP, ctypes.c_int]
         L.fp_batch_last_error.argtypes = [_VP]
         L.fp_batch_last_error.restype = ctypes.c_char_p
         L.fp_batch_free.argtypes = [_VP]
@@ -271,10 +270,6 @@ def fp_batch_rhs(batch, dqdt_ptrs, stream=0):
 
 def fp_batch_launches_per_step(batch):
     return lib().fp_batch_launches_per_step(batch)
-
-
-def fp_batch_lines_per_thread(batch, direction):
-    return lib().fp_batch_lines_per_thread(batch, int(direction))
 
 
 def fp_batch_free(batch):

@@ -43,7 +43,6 @@ struct fp_ctx {
   int2 *items[3] = {nullptr, nullptr, nullptr};
   int nitems[3] = {0, 0, 0};
   int per_sm = 1;
-  int per_sm2 = 1;                    // resident CTAs per SM of the two-lines-per-thread sweep
   int nsm = 152;
   int dev = 0;                        // the device the context's memory lives on
   double dt_host = 0.0;
@@ -70,8 +69,7 @@ struct fp_batch {
   int nbranch = 1;
   int2 *bitems[kMaxBranch][3] = {};
   int bnitems[kMaxBranch][3] = {};
-  int per_sm = 1, per_sm2 = 1, nsm = 152;
-  int lpt[3] = {1, 1, 1};   // lines per thread of every block in direction d
+  int per_sm = 1, nsm = 152;
   int2 *lam_items = nullptr;
   int nlam_items = 0;
   std::string err;
@@ -198,16 +196,8 @@ int prepare(int is_f32, int M, int scheme) {
 
 cudaError_t launch(int is_f32, const fpk::SweepLaunch &L, int M, int scheme, int charwise, int fp,
                    cudaStream_t s) {
-  if (L.lpt == 2) return fpk::launch_sweep2_f32(L, M, scheme, charwise, fp, s);
   return is_f32 ? fpk::launch_sweep_f32(L, M, scheme, charwise, fp, s)
                 : fpk::launch_sweep_f64(L, M, scheme, charwise, fp, s);
-}
-
-// the two-lines-per-thread sweep serves FP32 WENO5-JS and linear upwind in directions
-// without slip-wall, cut, block-link or halo sides
-int lpt_eligible(const fp_grid_desc &d, int dir) {
-  return d.precision == FP_F32_MIXED && (d.scheme == FP_WENO5_JS || d.scheme == FP_LINEAR_UPWIND5) &&
-         dir < d.dims && !has_bnd(d, dir);
 }
 
 void default_tile(int dir, int nd, int *S, int *TT) {
@@ -269,7 +259,6 @@ void fill_dirs(fp_ctx *c) {
     }
     if (d < dims) default_tile(d, D.nd, &D.S, &D.TT);
     else { D.S = 8; D.TT = 32; D.nlines = 0; }
-    D.lpt = lpt_eligible(c->desc, d) ? 2 : 1;
   }
   B.dims = dims;
   B.G = G;
@@ -291,7 +280,7 @@ void fill_dirs(fp_ctx *c) {
 
 void make_items(const BlockDev &B, int bidx, int d, std::vector<int2> &out) {
   const DirDev &D = B.dir[d];
-  for (long long L0 = 0; L0 < D.nlines; L0 += (long long)D.TT * D.lpt) out.push_back(make_int2(bidx, (int)L0));
+  for (long long L0 = 0; L0 < D.nlines; L0 += D.TT) out.push_back(make_int2(bidx, (int)L0));
 }
 
 int upload_items(fp_ctx *c) {
@@ -496,8 +485,6 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
   }
   fill_dirs(c);
   c->per_sm = prepare(c->is_f32, M, desc->scheme);
-  if (c->is_f32 && (desc->scheme == FP_WENO5_JS || desc->scheme == FP_LINEAR_UPWIND5))
-    c->per_sm2 = fpk::prepare_sweep2_f32(M, desc->scheme);
   FP_TRY(cudaGetLastError(), "prepare sweep kernels");
   int st = upload_items(c);
   if (st != FP_OK) { fp_free(c); return st; }
@@ -524,8 +511,7 @@ static int run_stage(fp_ctx *c, int stage, int rk, cudaStream_t s) {
     L.mode = d == 0 ? fpk::MODE_WRITE : (d == dims - 1 ? (rk ? fpk::MODE_RK : fpk::MODE_RHS) : fpk::MODE_ADD);
     L.stage = stage;
     L.dt = c->dt_dev;
-    L.lpt = c->hblk.dir[d].lpt;
-    L.grid = grid_for(L.lpt == 2 ? c->per_sm2 : c->per_sm, c->nsm, L.nitems);
+    L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
     L.bnd = has_bnd(c->desc, d);
     cudaError_t e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic,
                            c->desc.free_stream_preserving, s);
@@ -696,22 +682,17 @@ int fp_launches_per_step(const fp_ctx *c) { return c ? 3 * fp_launches_per_rhs(c
 int fp_get_tile(const fp_ctx *c, int dir, int *faces, int *lines) {
   if (!c || dir < 0 || dir > 2 || !faces || !lines) return FP_ERR_ARG;
   *faces = c->hblk.dir[dir].S;
-  *lines = c->hblk.dir[dir].TT * c->hblk.dir[dir].lpt;
+  *lines = c->hblk.dir[dir].TT;
   return FP_OK;
 }
 
 int fp_set_tile(fp_ctx *c, int dir, int faces, int lines) {
   if (!c) return FP_ERR_ARG;
   if (dir < 0 || dir >= c->desc.dims) return fail(c, FP_ERR_ARG, "fp_set_tile: bad direction");
-  const int per_thread = faces * lines == fpk::kThreads ? 1 : (faces * lines == 2 * fpk::kThreads ? 2 : 0);
-  if (!(faces == 8 || faces == 16 || faces == 32) || per_thread == 0)
-    return fail(c, FP_ERR_ARG, "fp_set_tile: faces in {8,16,32} and faces*lines == 256 or 512");
-  if (per_thread == 2 && !lpt_eligible(c->desc, dir))
-    return fail(c, FP_ERR_ARG, "fp_set_tile: two lines per thread needs the FP32 WENO5-JS or linear-upwind sweep "
-                               "and no slip-wall, cut, link or halo side in that direction");
+  if (!(faces == 8 || faces == 16 || faces == 32) || faces * lines != fpk::kThreads)
+    return fail(c, FP_ERR_ARG, "fp_set_tile: faces in {8,16,32} and faces*lines == 256");
   c->hblk.dir[dir].S = faces;
-  c->hblk.dir[dir].TT = lines / per_thread;
-  c->hblk.dir[dir].lpt = per_thread;
+  c->hblk.dir[dir].TT = lines;
   return upload_items(c);
 }
 
@@ -735,10 +716,6 @@ void fp_batch_free(fp_batch *b) {
 
 const char *fp_batch_last_error(const fp_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
-int fp_batch_lines_per_thread(const fp_batch *b, int dir) {
-  return (b && dir >= 0 && dir < 3) ? b->lpt[dir] : 0;
-}
-
 int fp_batch_launches_per_step(const fp_batch *b) {
   return b ? b->nbranch * 3 * (b->dims + (b->global_lf ? 2 : 0)) : 0;
 }
@@ -755,9 +732,8 @@ static int batch_items_into(fp_batch *b, int d, const std::vector<int> *only_blo
     if (only_blocks && std::find(only_blocks->begin(), only_blocks->end(), (int)k) == only_blocks->end())
       continue;
     const DirDev &D = b->hblk[k].dir[d];
-    const long long step = (long long)D.TT * D.lpt;
-    for (long long L0 = 0; L0 < D.nlines; L0 += step) {
-      long long lines = std::min<long long>(step, D.nlines - L0);
+    for (long long L0 = 0; L0 < D.nlines; L0 += D.TT) {
+      long long lines = std::min<long long>(D.TT, D.nlines - L0);
       work.push_back({(long long)D.nd * lines, make_int2((int)k, (int)L0)});
     }
   }
@@ -798,8 +774,7 @@ static int batch_pass_items(fp_batch *b, int d, int mode, int stage, cudaStream_
   L.mode = mode;
   L.stage = stage;
   L.dt = b->dt_dev;
-  L.lpt = b->lpt[d];
-  L.grid = grid_for(L.lpt == 2 ? b->per_sm2 : b->per_sm, b->nsm, L.nitems);
+  L.grid = grid_for(b->per_sm, b->nsm, L.nitems);
   L.bnd = b->bnd[d];
   cudaError_t e = launch(b->is_f32, L, b->M, b->scheme, b->charwise, b->fp, s);
   if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
@@ -898,15 +873,10 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
   b->is_f32 = d0.precision == FP_F32_MIXED;
   b->global_lf = d0.global_lf;
   b->per_sm = blocks[0]->per_sm;
-  b->per_sm2 = blocks[0]->per_sm2;
   b->nsm = blocks[0]->nsm;
-  for (int d = 0; d < 3; ++d) b->lpt[d] = 2;
   for (int k = 0; k < nblocks; ++k) {
     b->ctx.push_back(blocks[k]);
     for (int d = 0; d < 3; ++d) b->bnd[d] |= has_bnd(blocks[k]->desc, d);
-    // one launch covers every block of a pass: two lines per thread only if all blocks can
-    for (int d = 0; d < 3; ++d)
-      if (!lpt_eligible(blocks[k]->desc, d)) b->lpt[d] = 1;
     BlockDev B = blocks[k]->hblk;
     B.q[0] = q_devs[k];
     B.dqdt = nullptr;
@@ -914,10 +884,6 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
       for (int sd = 0; sd < 2; ++sd) B.nbr[d][sd] = nbr[(size_t)k * 6 + d * 2 + sd];
     b->hblk.push_back(B);
   }
-  for (int d = 0; d < 3; ++d)
-    if (b->bnd[d] || d >= b->dims) b->lpt[d] = 1;
-  for (auto &B : b->hblk)        // S x TT stays 256 threads in either layout
-    for (int d = 0; d < 3; ++d) B.dir[d].lpt = b->lpt[d];
   cudaError_t e = fpk::dev_alloc(&b->dblk, nblocks * sizeof(BlockDev));
   if (e == cudaSuccess) e = fpk::dev_alloc(&b->dt_dev, sizeof(double));
   if (e == cudaSuccess) e = fpk::host_malloc(reinterpret_cast<void **>(&b->dt_host), sizeof(double));
@@ -1101,8 +1067,7 @@ extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream
     L.mode = d == 0 ? fpk::MODE_WRITE : (d == dims - 1 ? fpk::MODE_RHS : fpk::MODE_ADD);
     L.stage = 0;
     L.dt = c->dt_dev;
-    L.lpt = c->hblk.dir[d].lpt;
-    L.grid = grid_for(L.lpt == 2 ? c->per_sm2 : c->per_sm, c->nsm, L.nitems);
+    L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
     L.bnd = has_bnd(c->desc, d);
     e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic, c->desc.free_stream_preserving, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: sweep launch");

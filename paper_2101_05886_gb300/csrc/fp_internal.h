@@ -40,8 +40,7 @@ struct DirDev {
   long long fT1, fT2, fsd;  // face-metric offsets, face f+1/2 at (f+1)*fsd
   long long fc;        // face-metric component stride
   int bclo, bchi;      // boundary codes at the two line ends
-  int S, TT;           // faces per chunk, lines (or line pairs) per tile (S * TT == kThreads)
-  int lpt;             // grid lines per thread: 1 (fp_sweep) or 2 (fp_sweep2, FP32 WENO5/linear upwind)
+  int S, TT;           // faces per chunk, lines per tile (S * TT == kThreads)
   const void *fmet;    // T [3][faces]
   const void *dk;      // T [3][cells]: k_{i+1/2} - k_{i-1/2} along this direction (FP64-formed)
   // FP_BC_HALO sides: the caller's buffers of the G cells beyond each side, laid out like the
@@ -82,7 +81,6 @@ struct SweepLaunch {
   const double *dt;    // device scalar
   int grid;            // CTAs of the persistent launch
   int bnd;             // some block of the launch has a slip-wall or cut side in `dir`
-  int lpt;             // lines per thread of every block of the launch in `dir` (1 or 2)
 };
 
 // Launchers (sweep_f32.cu / sweep_f64.cu).  Return cudaError_t of the launch.
@@ -94,9 +92,6 @@ cudaError_t launch_sweep_f32(const SweepLaunch &L, int M, int scheme, int charwi
 // return the resident CTAs per SM of the given variant.
 int prepare_sweep_f64(int M, int scheme);
 int prepare_sweep_f32(int M, int scheme);
-// the two-lines-per-thread FP32 sweep (sweep2_f32.cu): schemes 0 and 1, no boundary-rule sides
-cudaError_t launch_sweep2_f32(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
-int prepare_sweep2_f32(int M, int scheme);
 // variants with the slip-wall / cut rules compiled in (sweep_f32_bnd.cu, sweep_f64_bnd.cu)
 cudaError_t launch_sweep_f64_bnd(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
                                  cudaStream_t s);

@@ -109,9 +109,6 @@ class Batch:
     def launches_per_step(self):
         return B.fp_batch_launches_per_step(self.batch)
 
-    def lines_per_thread(self):
-        return [B.fp_batch_lines_per_thread(self.batch, d) for d in range(3)]
-
     def close(self):
         if self.batch:
             B.fp_batch_free(self.batch)

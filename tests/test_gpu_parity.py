@@ -904,47 +904,3 @@ def test_full_size_cgrid_sampled_parity():
         err = subbox_err(got, g, q, M, lo, np.array((6, 6, 6)), qinf=qinf)
         assert err <= 1e-5, (lo, err)
     blk.close()
-
-
-# ---- the two-lines-per-thread FP32 sweep against the one-line sweep and the oracle ----
-@pytest.mark.parametrize("name,M,scheme,charwise", [("3d_vortex", 6, 0, 1), ("3d_vortex", 6, 1, 1), ("3d_ogrid", 4, 0, 1),
-                                                    ("3d_ogrid", 8, 1, 0), ("2d_vortex", 6, 0, 1), ("3d_min", 6, 1, 1)])
-def test_two_line_sweep_is_as_accurate_as_the_one_line_sweep(name, M, scheme, charwise):
-    """FP32 WENO5-JS and linear upwind run by default with two grid lines per thread (every
-    face operation packed across the two lines); the same blocks with one line per thread
-    (fp_set_tile with faces x lines = 256) evaluate the same algebra grouped differently.
-    Both residuals are within 1e-5 of the oracle and within 2e-5 of each other (two FP32
-    evaluations; measured up to 5e-6 apart), and two RK3 steps of either layout are as close
-    to the FP64 sweep's steps as the other's (the O-grid's residual is ill conditioned, so
-    the two FP32 step sequences drift apart by up to 3e-5 while each stays as close to FP64).
-    The cases include odd line counts (a thread whose second line is missing)."""
-    g, qinf, q = _case(name, M)
-    q, qinf = f32(q), f32(qinf)
-    two = Block(g, metric_order=M, scheme=scheme, characteristic=charwise, precision=F32, q_inf=qinf)
-    one = Block(g, metric_order=M, scheme=scheme, characteristic=charwise, precision=F32, q_inf=qinf)
-    ref = Block(g, metric_order=M, scheme=scheme, characteristic=charwise, precision=F64, q_inf=qinf)
-    for d in range(g.dims):
-        faces, lines = B.fp_get_tile(two.ctx, d)
-        assert faces * lines == 512                     # two lines per thread by default
-        B.fp_set_tile(one.ctx, d, faces, 256 // faces)
-        assert B.fp_get_tile(one.ctx, d) == (faces, 256 // faces)
-    qd = two.to_device(q)
-    d2, d1 = two.rhs(qd).cpu().numpy(), one.rhs(qd).cpu().numpy()
-    cfg = O.cfg_for(g, M=M, scheme=scheme, charwise=charwise, qinf=qinf)
-    P = Parity(cfg, O.metrics(cfg, g.nodes, g.Gn), q)
-    assert P.err(d2) <= 1e-5 and P.err(d1) <= 1e-5
-    assert residual_err(-d2 * P.invJ, -d1 * P.invJ, P.tau) <= 2e-5
-    q2, q1, q64 = two.to_device(q), one.to_device(q), ref.to_device(q)
-    dt = 0.5 * ref.cfl_dt(q64, 0.5)
-    for _ in range(2):
-        two.rk3_step(q2, dt)
-        one.rk3_step(q1, dt)
-        ref.rk3_step(q64, dt)
-    torch.cuda.synchronize()
-    inc64 = q64.cpu().numpy() - q
-    e2 = state_err(q2.cpu().numpy().astype(np.float64) - q, inc64)
-    e1 = state_err(q1.cpu().numpy().astype(np.float64) - q, inc64)
-    assert e2 <= max(2.0 * e1, 1e-5), (e2, e1)
-    assert two.status() == B.FP_OK and one.status() == B.FP_OK
-    for b in (two, one, ref):
-        b.close()
