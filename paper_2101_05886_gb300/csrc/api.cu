@@ -190,14 +190,31 @@ int has_halo(const fp_grid_desc &d) {
 
 int ghost_of(int M, int scheme) { return std::max(scheme == FP_WENO7_JS ? 4 : 3, M / 2); }
 
+// resident CTAs per SM of the sweep (the fewest over its variants), after opting every
+// variant in to its dynamic shared memory
 int prepare(int is_f32, int M, int scheme) {
-  return is_f32 ? fpk::prepare_sweep_f32(M, scheme) : fpk::prepare_sweep_f64(M, scheme);
+  using P = int (*)(int, int);
+  const P f32[4] = {fpk::prepare_sweep_f32, fpk::prepare_sweep_f32_fix, fpk::prepare_sweep_f32_bnd,
+                    fpk::prepare_sweep_f32_bnd_fix};
+  const P f64[4] = {fpk::prepare_sweep_f64, fpk::prepare_sweep_f64_fix, fpk::prepare_sweep_f64_bnd,
+                    fpk::prepare_sweep_f64_bnd_fix};
+  int nb = 1 << 20;
+  for (P p : is_f32 ? f32 : f64) nb = std::min(nb, p(M, scheme));
+  return nb;
 }
 
+// the variant of the launch: boundary rules compiled in when some block of the launch has such a
+// side in its direction, the switches folded when both are on (not for WENOCU6, whose sweep
+// measured 1 % slower with them folded)
 cudaError_t launch(int is_f32, const fpk::SweepLaunch &L, int M, int scheme, int charwise, int fp,
                    cudaStream_t s) {
-  return is_f32 ? fpk::launch_sweep_f32(L, M, scheme, charwise, fp, s)
-                : fpk::launch_sweep_f64(L, M, scheme, charwise, fp, s);
+  using F = cudaError_t (*)(const fpk::SweepLaunch &, int, int, int, int, cudaStream_t);
+  const F f32[4] = {fpk::launch_sweep_f32, fpk::launch_sweep_f32_fix, fpk::launch_sweep_f32_bnd,
+                    fpk::launch_sweep_f32_bnd_fix};
+  const F f64[4] = {fpk::launch_sweep_f64, fpk::launch_sweep_f64_fix, fpk::launch_sweep_f64_bnd,
+                    fpk::launch_sweep_f64_bnd_fix};
+  const int v = (L.bnd ? 2 : 0) + (charwise && fp && scheme != FP_WENOCU6 ? 1 : 0);
+  return (is_f32 ? f32 : f64)[v](L, M, scheme, charwise, fp, s);
 }
 
 void default_tile(int dir, int nd, int *S, int *TT) {

@@ -83,22 +83,27 @@ struct SweepLaunch {
   int bnd;             // some block of the launch has a slip-wall or cut side in `dir`
 };
 
-// Launchers (sweep_f32.cu / sweep_f64.cu).  Return cudaError_t of the launch.
-cudaError_t launch_sweep_f64(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
-                             cudaStream_t s);
-cudaError_t launch_sweep_f32(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
-                             cudaStream_t s);
-// Opt in to the sweep's dynamic shared memory (all variants of one precision) and
-// return the resident CTAs per SM of the given variant.
-int prepare_sweep_f64(int M, int scheme);
+// Launchers of the sweep, one per translation unit (sweep_<NAME>.cu): precision f32 / f64,
+// `_bnd` with the slip-wall, cut, link and halo rules compiled in, `_fix` with the
+// characteristic decomposition and the FP form fixed on.  Each returns the cudaError_t of the
+// launch; prepare_sweep_<NAME> opts in to the dynamic shared memory of its 16 (M, scheme)
+// variants and returns the resident CTAs per SM of the given one.
+cudaError_t launch_sweep_f32(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
+cudaError_t launch_sweep_f32_fix(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
+cudaError_t launch_sweep_f32_bnd(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
+cudaError_t launch_sweep_f32_bnd_fix(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
+cudaError_t launch_sweep_f64(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
+cudaError_t launch_sweep_f64_fix(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
+cudaError_t launch_sweep_f64_bnd(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
+cudaError_t launch_sweep_f64_bnd_fix(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
 int prepare_sweep_f32(int M, int scheme);
-// variants with the slip-wall / cut rules compiled in (sweep_f32_bnd.cu, sweep_f64_bnd.cu)
-cudaError_t launch_sweep_f64_bnd(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
-                                 cudaStream_t s);
-cudaError_t launch_sweep_f32_bnd(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
-                                 cudaStream_t s);
-int prepare_sweep_f64_bnd(int M, int scheme);
+int prepare_sweep_f32_fix(int M, int scheme);
 int prepare_sweep_f32_bnd(int M, int scheme);
+int prepare_sweep_f32_bnd_fix(int M, int scheme);
+int prepare_sweep_f64(int M, int scheme);
+int prepare_sweep_f64_fix(int M, int scheme);
+int prepare_sweep_f64_bnd(int M, int scheme);
+int prepare_sweep_f64_bnd_fix(int M, int scheme);
 
 // Every device and page-locked allocation of the library goes through these two, so the
 // host-side hook fp_debug_fail_allocation can make a chosen one fail as if the device (or

@@ -343,10 +343,15 @@ __device__ __forceinline__ void dflux_pair(T g1, typename PairOf<T>::type rinvB,
   out[4] = pfma(pc<P>(EA + pA), dU, pmul(padd(d[4], dp), UB));
 }
 
-template <typename T, int M, int SCHEME, bool BND>
+// FIX = 1: the characteristic decomposition and the FP form are fixed on at compile time (the
+// configuration of every workload of the paper), so their switches fold away; FIX = 0 reads them
+// from the arguments.
+template <typename T, int M, int SCHEME, bool BND, int FIX>
 __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && SCHEME != 2 ? 2 : 1))
 fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, int nitems, int dir,
-         int mode, int stage, const double *__restrict__ dtp, int charwise, int fpform) {
+         int mode, int stage, const double *__restrict__ dtp, int charwise_arg, int fpform_arg) {
+  const int charwise = FIX ? 1 : charwise_arg;
+  const int fpform = FIX ? 1 : fpform_arg;
   // stencil points of a face: i-2..i+3 (5th order) or i-3..i+4 (WENO7), offset index Q0
   constexpr int NS = SCHEME == 2 ? 8 : 6;
   constexpr int Q0 = SCHEME == 2 ? 0 : 1;
@@ -1019,20 +1024,20 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
   }
 }
 
-template <typename T, int M, int SCHEME, bool BND>
+template <typename T, int M, int SCHEME, bool BND, int FIX>
 cudaError_t launch_one(const SweepLaunch &L, int charwise, int fp, cudaStream_t s) {
   const size_t smem = ((size_t)(kCellFields + kFaceFields) * kRing + (size_t)(kNextFields + kEpiFields) * kThreads) * sizeof(T);
   if (L.nitems <= 0) return cudaSuccess;
-  fp_sweep<T, M, SCHEME, BND><<<L.grid, kThreads, smem, s>>>(L.blocks, L.items, L.nitems, L.dir, L.mode,
-                                                      L.stage, L.dt, charwise, fp);
+  fp_sweep<T, M, SCHEME, BND, FIX><<<L.grid, kThreads, smem, s>>>(L.blocks, L.items, L.nitems, L.dir, L.mode,
+                                                           L.stage, L.dt, charwise, fp);
   return cudaGetLastError();
 }
 
-template <typename T, bool BND>
+template <typename T, bool BND, int FIX>
 cudaError_t launch_sweep_t(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
                            cudaStream_t s) {
 #define FPK_CASE(MM, SS) \
-  if (M == MM && scheme == SS) return launch_one<T, MM, SS, BND>(L, charwise, fp, s);
+  if (M == MM && scheme == SS) return launch_one<T, MM, SS, BND, FIX>(L, charwise, fp, s);
   FPK_CASE(2, 0) FPK_CASE(4, 0) FPK_CASE(6, 0) FPK_CASE(8, 0)
   FPK_CASE(2, 1) FPK_CASE(4, 1) FPK_CASE(6, 1) FPK_CASE(8, 1)
   FPK_CASE(2, 2) FPK_CASE(4, 2) FPK_CASE(6, 2) FPK_CASE(8, 2)
@@ -1043,16 +1048,16 @@ cudaError_t launch_sweep_t(const SweepLaunch &L, int M, int scheme, int charwise
 
 // Opt in to the dynamic shared memory of every variant and return the resident
 // CTAs per SM of the requested one.  Called before any launch or graph capture.
-template <typename T, bool BND>
+template <typename T, bool BND, int FIX>
 int prepare_t(int M, int scheme) {
   const size_t smem = ((size_t)(kCellFields + kFaceFields) * kRing + (size_t)(kNextFields + kEpiFields) * kThreads) * sizeof(T);
   int nb = 0;
 #define FPK_OCC(MM, SS)                                                                              \
   {                                                                                                  \
-    cudaFuncSetAttribute(fp_sweep<T, MM, SS, BND>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+    cudaFuncSetAttribute(fp_sweep<T, MM, SS, BND, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                          (int)smem);                                                                 \
     if (M == MM && scheme == SS)                                                                     \
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fp_sweep<T, MM, SS, BND>, kThreads, smem);   \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fp_sweep<T, MM, SS, BND, FIX>, kThreads, smem); \
   }
   FPK_OCC(2, 0) FPK_OCC(4, 0) FPK_OCC(6, 0) FPK_OCC(8, 0)
   FPK_OCC(2, 1) FPK_OCC(4, 1) FPK_OCC(6, 1) FPK_OCC(8, 1)
@@ -1061,5 +1066,14 @@ int prepare_t(int M, int scheme) {
 #undef FPK_OCC
   return nb > 0 ? nb : 1;
 }
+
+// One translation unit per (precision, boundary rules, fixed switches): the launcher and the
+// preparation of its 16 (M, scheme) variants, named launch_sweep_<NAME> / prepare_sweep_<NAME>.
+#define FPK_SWEEP_UNIT(NAME, T, BND, FIX)                                                           \
+  cudaError_t launch_sweep_##NAME(const SweepLaunch &L, int M, int scheme, int charwise, int fp,    \
+                                  cudaStream_t s) {                                                 \
+    return launch_sweep_t<T, BND, FIX>(L, M, scheme, charwise, fp, s);                              \
+  }                                                                                                 \
+  int prepare_sweep_##NAME(int M, int scheme) { return prepare_t<T, BND, FIX>(M, scheme); }
 
 }  // namespace fpk

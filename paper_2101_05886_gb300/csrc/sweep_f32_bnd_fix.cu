@@ -1,0 +1,7 @@
+// sweep_f32_bnd_fix.cu - FP32 residual sweep with the slip-wall, cut, link and halo rules compiled in,
+// characteristic decomposition and FP form fixed on at compile time.
+#include "sweep.cuh"
+
+namespace fpk {
+FPK_SWEEP_UNIT(f32_bnd_fix, float, true, 1)
+}  // namespace fpk

@@ -1,11 +1,7 @@
-// sweep_f64_bnd.cu - FP64 instantiations of the residual sweep with the slip-wall and
-// C-grid cut boundary rules compiled in.
+// sweep_f64_bnd.cu - FP64 residual sweep with the slip-wall, cut, link and halo rules compiled in,
+// switches read at run time.
 #include "sweep.cuh"
 
 namespace fpk {
-cudaError_t launch_sweep_f64_bnd(const SweepLaunch &L, int M, int scheme, int charwise, int fp,
-                                 cudaStream_t s) {
-  return launch_sweep_t<double, true>(L, M, scheme, charwise, fp, s);
-}
-int prepare_sweep_f64_bnd(int M, int scheme) { return prepare_t<double, true>(M, scheme); }
+FPK_SWEEP_UNIT(f64_bnd, double, true, 0)
 }  // namespace fpk
