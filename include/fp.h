@@ -285,8 +285,14 @@ int fp_pipe_create(fp_ctx *const *blocks, int nblocks, const void *const *q_host
    is synchronised.  The pipe's work is not ordered after work the caller queued earlier on
    `stream`, so the pipe's contexts (and their stage and residual scratch) must not be used by
    other calls (fp_rhs, fp_rk3_step, a batch) while a pipe step may be in flight: synchronise
-   `stream` before such a call. */
+   `stream` before such a call, or switch the pipe to ordered steps (fp_pipe_set_ordered). */
 int fp_pipe_rk3_step_host(fp_pipe *pipe, void *const *q_host, double dt, void *stream);
+/* Ordered steps (ordered nonzero): every step of the pipe also follows the work queued on the
+   step's `stream` before the call, as a call on one stream would, so that work may fill the host
+   states (a device-to-host copy, a host function) or use the pipe's contexts.  The price is the
+   overlap of consecutive steps: a step's first uploads then wait for the previous step's last
+   group.  Off (0) by default.  FP_ERR_ARG for a NULL pipe. */
+int fp_pipe_set_ordered(fp_pipe *pipe, int ordered);
 int fp_pipe_groups(const fp_pipe *pipe);
 int fp_pipe_launches_per_step(const fp_pipe *pipe);
 const char *fp_pipe_last_error(const fp_pipe *pipe);

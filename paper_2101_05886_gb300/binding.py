@@ -25,7 +25,7 @@ EXPORTS = [
     "fp_launches_per_step", "fp_get_tile", "fp_set_tile", "fp_last_error", "fp_status_string",
     "fp_free", "fp_batch_create", "fp_batch_create_linked", "fp_batch_rk3_step", "fp_batch_rhs", "fp_batch_launches_per_step",
     "fp_batch_last_error", "fp_batch_free", "fp_state_bytes", "fp_pipe_create", "fp_pipe_rk3_step_host",
-    "fp_pipe_groups", "fp_pipe_launches_per_step", "fp_pipe_last_error", "fp_pipe_free",
+    "fp_pipe_set_ordered", "fp_pipe_groups", "fp_pipe_launches_per_step", "fp_pipe_last_error", "fp_pipe_free",
     "fp_balanced_groups", "fp_debug_fail_allocation", "fp_probe_peaks", "fp_rk3_stage", "fp_set_halo",
     "fp_halo_bytes", "fp_pack_halo",
 ]
@@ -91,6 +91,7 @@ def lib():
         L.fp_pipe_create.argtypes = [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP), ctypes.c_int,
                                      ctypes.c_int, ctypes.POINTER(_VP)]
         L.fp_pipe_rk3_step_host.argtypes = [_VP, ctypes.POINTER(_VP), ctypes.c_double, _VP]
+        L.fp_pipe_set_ordered.argtypes = [_VP, ctypes.c_int]
         L.fp_pipe_groups.argtypes = [_VP]
         L.fp_pipe_launches_per_step.argtypes = [_VP]
         L.fp_pipe_last_error.argtypes = [_VP]
@@ -296,6 +297,12 @@ def fp_pipe_rk3_step_host(pipe, q_host_ptrs, dt, stream=0):
     st = lib().fp_pipe_rk3_step_host(pipe, qs, float(dt), stream)
     if st != FP_OK:
         raise FPError(st, lib().fp_pipe_last_error(pipe).decode())
+
+
+def fp_pipe_set_ordered(pipe, ordered):
+    st = lib().fp_pipe_set_ordered(pipe, int(ordered))
+    if st != FP_OK:
+        raise FPError(st, "fp_pipe_set_ordered")
 
 
 def fp_pipe_groups(pipe):

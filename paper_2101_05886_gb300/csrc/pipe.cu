@@ -26,6 +26,8 @@ struct fp_pipe {
   std::vector<fp_batch *> batch;            // one batch per group
   std::vector<cudaStream_t> st;             // one stream per group
   std::vector<cudaEvent_t> done;            // end of each group's step
+  cudaEvent_t start = nullptr;              // the caller's stream at the start of a step (ordered mode)
+  int ordered = 0;
   std::string err;
 };
 
@@ -50,6 +52,7 @@ void fp_pipe_free(fp_pipe *p) {
     if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : p->done)
     if (e) cudaEventDestroy(e);
+  if (p->start) cudaEventDestroy(p->start);
   delete p;
 }
 
@@ -83,7 +86,7 @@ int fp_pipe_create(fp_ctx *const *blocks, int nblocks, const void *const *q_host
       return e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA;
     }
   }
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaEventCreateWithFlags(&p->start, cudaEventDisableTiming);
   for (int g = 0; g < ngroups && e == cudaSuccess; ++g) {
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
@@ -122,10 +125,13 @@ int fp_pipe_rk3_step_host(fp_pipe *p, void *const *q_host, double dt, void *stre
     if (!q_host[k]) return pipe_fail(p, FP_ERR_ARG, "fp_pipe_rk3_step_host: null state");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
+  // ordered mode: every group's work also follows what was queued on `stream` before the call
+  if (p->ordered) e = cudaEventRecord(p->start, s);
   // each group's work follows that group's previous step on its own stream, so one step's
   // first uploads overlap the previous step's last groups; `stream` waits for every group
   for (size_t g = 0; g < p->groups.size() && e == cudaSuccess; ++g) {
     cudaStream_t gs = p->st[g];
+    if (p->ordered) e = cudaStreamWaitEvent(gs, p->start, 0);
     for (int k : p->groups[g])
       if (e == cudaSuccess) e = cudaMemcpyAsync(p->qdev[k], q_host[k], p->bytes[k], cudaMemcpyHostToDevice, gs);
     if (e != cudaSuccess) break;
@@ -138,6 +144,12 @@ int fp_pipe_rk3_step_host(fp_pipe *p, void *const *q_host, double dt, void *stre
   }
   if (e != cudaSuccess)
     return pipe_fail(p, FP_ERR_CUDA, std::string("fp_pipe_rk3_step_host: ") + cudaGetErrorString(e));
+  return FP_OK;
+}
+
+int fp_pipe_set_ordered(fp_pipe *p, int ordered) {
+  if (!p) return FP_ERR_ARG;
+  p->ordered = ordered ? 1 : 0;
   return FP_OK;
 }
 

@@ -125,15 +125,18 @@ class Pipe:
     """Blocks whose states live in host memory (page-locked CPU tensors), advanced with
     the host<->device copies overlapped by compute (fp_pipe_*): the blocks are split into
     `groups` batches with a stream each.  Steps run on the pipe's own streams, so the blocks
-    must not be used by other calls while a step may be in flight (synchronise first)."""
+    must not be used by other calls while a step may be in flight (synchronise first), unless
+    `ordered` makes every step follow the work queued before it on the current stream."""
 
-    def __init__(self, blocks, host_states, groups=4, autotune=True):
+    def __init__(self, blocks, host_states, groups=4, autotune=True, ordered=False):
         self.blocks = list(blocks)
         self.host = list(host_states)
         for b, h in zip(self.blocks, self.host):
             assert h.device.type == "cpu" and h.is_contiguous() and tuple(h.shape) == b.shape and h.dtype == b.dtype
         self.pipe = B.fp_pipe_create([b.ctx for b in self.blocks], [h.data_ptr() for h in self.host],
                                      groups, int(autotune))
+        if ordered:
+            B.fp_pipe_set_ordered(self.pipe, 1)
 
     def rk3_step(self, dt: float):
         B.fp_pipe_rk3_step_host(self.pipe, [h.data_ptr() for h in self.host], dt, _stream())

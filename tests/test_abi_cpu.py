@@ -93,6 +93,7 @@ def test_pipe_and_link_calls_reject_null_arguments(lib):
     assert lib.fp_pipe_create(None, 1, None, 4, 0, ctypes.byref(out)) == B.FP_ERR_ARG
     assert lib.fp_pipe_create(None, 0, None, 4, 0, None) == B.FP_ERR_ARG
     assert lib.fp_pipe_rk3_step_host(None, None, 1e-3, None) == B.FP_ERR_ARG
+    assert lib.fp_pipe_set_ordered(None, 1) == B.FP_ERR_ARG
     assert lib.fp_pipe_groups(None) == 0
     assert lib.fp_pipe_launches_per_step(None) == 0
     lib.fp_pipe_free(None)

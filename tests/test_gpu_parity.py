@@ -844,6 +844,35 @@ def test_pipe_host_states_equal_the_device_batch():
         b.close()
 
 
+def test_ordered_pipe_sees_host_states_written_by_earlier_stream_work():
+    """With ordered steps (fp_pipe_set_ordered) a step follows the work queued before it on the
+    caller's stream: here a delay kernel and then device-to-host copies that overwrite the host
+    states.  The step must advance the overwritten states (as a device batch does from the same
+    data), not the values the host states held when the call was made."""
+    grids, qinf, blocks, states = _mini_batch(F32)
+    hosts = [q.cpu().pin_memory() for q in states]
+    from paper_2101_05886_gb300.solver import Pipe
+    pblocks = [Block(g, metric_order=6, precision=F32, q_inf=qinf) for g in grids]
+    pipe = Pipe(pblocks, hosts, groups=2, autotune=False, ordered=True)
+    new = [q * 1.01 for q in states]               # other (valid) states on the device
+    ref = [q.clone() for q in new]
+    torch.cuda.synchronize()
+    torch.cuda._sleep(50_000_000)                  # about 25 ms of the caller's stream
+    for h, q in zip(hosts, new):
+        h.copy_(q, non_blocking=True)              # device -> pinned host, on the caller's stream
+    pipe.rk3_step(1e-3)
+    torch.cuda.synchronize()
+    bat = Batch(blocks, ref, autotune=False)
+    bat.rk3_step(1e-3)
+    torch.cuda.synchronize()
+    for h, r in zip(hosts, ref):
+        assert torch.equal(h, r.cpu())
+    pipe.close()
+    bat.close()
+    for b in blocks + pblocks:
+        b.close()
+
+
 # ---- full-size parity in the benchmark's launch configuration ----
 def test_full_size_batched_workload_sampled_parity():
     """The 64-block batched workload at full size (34.5M points) with the benchmark's autotuned
