@@ -204,8 +204,8 @@ int prepare(int is_f32, int M, int scheme) {
 }
 
 // the variant of the launch: boundary rules compiled in when some block of the launch has such a
-// side in its direction, the switches folded when both are on (not for WENOCU6, whose sweep
-// measured 1 % slower with them folded)
+// side in its direction, the switches folded for characteristic FP sweeps with local speeds (not
+// for WENOCU6, whose sweep measured 1 % slower with them folded)
 cudaError_t launch(int is_f32, const fpk::SweepLaunch &L, int M, int scheme, int charwise, int fp,
                    cudaStream_t s) {
   using F = cudaError_t (*)(const fpk::SweepLaunch &, int, int, int, int, cudaStream_t);
@@ -213,7 +213,7 @@ cudaError_t launch(int is_f32, const fpk::SweepLaunch &L, int M, int scheme, int
                     fpk::launch_sweep_f32_bnd_fix};
   const F f64[4] = {fpk::launch_sweep_f64, fpk::launch_sweep_f64_fix, fpk::launch_sweep_f64_bnd,
                     fpk::launch_sweep_f64_bnd_fix};
-  const int v = (L.bnd ? 2 : 0) + (charwise && fp && scheme != FP_WENOCU6 ? 1 : 0);
+  const int v = (L.bnd ? 2 : 0) + (charwise && fp && !L.glf && scheme != FP_WENOCU6 ? 1 : 0);
   return (is_f32 ? f32 : f64)[v](L, M, scheme, charwise, fp, s);
 }
 
@@ -530,6 +530,7 @@ static int run_stage(fp_ctx *c, int stage, int rk, cudaStream_t s) {
     L.dt = c->dt_dev;
     L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
     L.bnd = has_bnd(c->desc, d);
+    L.glf = c->desc.global_lf;
     cudaError_t e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic,
                            c->desc.free_stream_preserving, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
@@ -793,6 +794,7 @@ static int batch_pass_items(fp_batch *b, int d, int mode, int stage, cudaStream_
   L.dt = b->dt_dev;
   L.grid = grid_for(b->per_sm, b->nsm, L.nitems);
   L.bnd = b->bnd[d];
+  L.glf = b->global_lf;
   cudaError_t e = launch(b->is_f32, L, b->M, b->scheme, b->charwise, b->fp, s);
   if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("batch sweep: ") + cudaGetErrorString(e));
   return FP_OK;
@@ -1086,6 +1088,7 @@ extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream
     L.dt = c->dt_dev;
     L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
     L.bnd = has_bnd(c->desc, d);
+    L.glf = c->desc.global_lf;
     e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic, c->desc.free_stream_preserving, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "fp_rhs_noalloc: sweep launch");
   }

@@ -81,6 +81,7 @@ struct SweepLaunch {
   const double *dt;    // device scalar
   int grid;            // CTAs of the persistent launch
   int bnd;             // some block of the launch has a slip-wall or cut side in `dir`
+  int glf;             // the blocks of the launch use global Lax-Friedrichs speeds
 };
 
 // Launchers of the sweep, one per translation unit (sweep_<NAME>.cu): precision f32 / f64,

@@ -343,9 +343,9 @@ __device__ __forceinline__ void dflux_pair(T g1, typename PairOf<T>::type rinvB,
   out[4] = pfma(pc<P>(EA + pA), dU, pmul(padd(d[4], dp), UB));
 }
 
-// FIX = 1: the characteristic decomposition and the FP form are fixed on at compile time (the
-// configuration of every workload of the paper), so their switches fold away; FIX = 0 reads them
-// from the arguments.
+// FIX = 1: the characteristic decomposition and the FP form on, local Lax-Friedrichs speeds,
+// all fixed at compile time (the configuration of the paper's workloads but the shock test), so
+// their switches fold away; FIX = 0 reads them from the arguments and the block descriptor.
 template <typename T, int M, int SCHEME, bool BND, int FIX>
 __global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && SCHEME != 2 ? 2 : 1))
 fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, int nitems, int dir,
@@ -396,7 +396,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     if (tid == 0 && nit < nitems) cp_async8(&s_item[cur ^ 1], items + nit);
     if (tid == 0) {                      // read after the prologue's barrier
       s_dt = mode == MODE_RK ? T(*dtp) : T(0);
-      if (B->global_lf)
+      if (!FIX && B->global_lf)
         for (int c = 0; c < 3; ++c) s_lam[c] = static_cast<const T *>(B->lamg)[3 * dir + c];
     }
     const int S = D->S, TT = D->TT, W = 2 * S;
@@ -425,7 +425,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     const T *__restrict__ fmet = static_cast<const T *>(D->fmet) + fbase;
     const T *__restrict__ qin = static_cast<const T *>(B->q[stage]);
     const T g1 = T(B->gamma - 1.0), gam = T(B->gamma);
-    const int glf = B->global_lf;
+    const int glf = FIX ? 0 : B->global_lf;
     T qb[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qb[v] = T(B->qbar[v]);
@@ -631,16 +631,27 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
 
         // reference face state Q* = Q_i + delta (Eqs. Q_star, QdJ_star, 1dJ at order M)
         T dl[5] = {T(0), T(0), T(0), T(0), T(0)};
+        // linear upwind with the switches folded keeps the cells' Q_q - Q_i and (1/J)_q of this
+        // loop for its stencil differences instead of loading them again (M6: 36 shared loads)
+        constexpr bool kKeep = SCHEME == 1 && FIX == 1;
+        constexpr int kQlo = 3 - M / 2 + 1, kQhi = kQlo + M;     // cells q of the weighted sum
+        T dqk[8][5], ijk[8];
         if (fpform) {
           T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
           T wsum = T(0);
 #pragma unroll
           for (int m = 0; m < M; ++m) {
-            const int q = 3 - M / 2 + 1 + m;
-            const T w = T(MidW<M>::w(m)) * CELL(CF_INVJ, q);
+            const int q = kQlo + m;
+            const T ij = CELL(CF_INVJ, q);
+            const T w = T(MidW<M>::w(m)) * ij;
             wsum += w;
+            if (kKeep) ijk[q] = ij;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) acc[v] += w * (CELL(CF_Q + v, q) - Qi[v]);
+            for (int v = 0; v < 5; ++v) {
+              const T dq = CELL(CF_Q + v, q) - Qi[v];
+              if (kKeep) dqk[q][v] = dq;
+              acc[v] += w * dq;
+            }
           }
           const T wi = Num<T>::rcp(wsum);
 #pragma unroll
@@ -689,13 +700,24 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         const T bb = g1 * csi * csi;
         const T knr = Num<T>::rsqrt_(kf[0] * kf[0] + kf[1] * kf[1] + kf[2] * kf[2]);
         const T n[3] = {kf[0] * knr, kf[1] * knr, kf[2] * knr};
+        // first tangent, normalised: e_z x n where n is far from e_z, else n x e_x.  Chosen by
+        // selects (faster for linear upwind and WENO7), except in the folded WENO5 sweep, where
+        // the selects cost registers and a branch measured faster.
         T t1[3], t2[3];
-        if (n[2] * n[2] <= T(0.5)) {
-          const T s = Num<T>::rsqrt_(n[0] * n[0] + n[1] * n[1]);
-          t1[0] = -n[1] * s; t1[1] = n[0] * s; t1[2] = T(0);
+        const bool lowz = n[2] * n[2] <= T(0.5);
+        if constexpr (SCHEME == 0 && FIX == 1) {
+          if (lowz) {
+            const T s = Num<T>::rsqrt_(n[0] * n[0] + n[1] * n[1]);
+            t1[0] = -n[1] * s; t1[1] = n[0] * s; t1[2] = T(0);
+          } else {
+            const T s = Num<T>::rsqrt_(n[1] * n[1] + n[2] * n[2]);
+            t1[0] = T(0); t1[1] = n[2] * s; t1[2] = -n[1] * s;
+          }
         } else {
-          const T s = Num<T>::rsqrt_(n[1] * n[1] + n[2] * n[2]);
-          t1[0] = T(0); t1[1] = n[2] * s; t1[2] = -n[1] * s;
+          const T s = Num<T>::rsqrt_(lowz ? n[0] * n[0] + n[1] * n[1] : n[1] * n[1] + n[2] * n[2]);
+          t1[0] = lowz ? -n[1] * s : T(0);
+          t1[1] = (lowz ? n[0] : n[2]) * s;
+          t1[2] = lowz ? T(0) : -n[1] * s;
         }
         t2[0] = n[1] * t1[2] - n[2] * t1[1];
         t2[1] = n[2] * t1[0] - n[0] * t1[2];
@@ -765,11 +787,14 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           for (int s = 0; s < 3; ++s) {
             const int q = s + 1, q2 = 6 - s;
             P dp[5], out[5];
+            // both cells among those of the weighted sum (all of them at M6)
+            const bool kept = kKeep && q >= kQlo && q2 < kQhi;
             if (fpform) {
               P kp2[3], uBp[3];
 #pragma unroll
               for (int v = 0; v < 5; ++v)
-                dp[v] = psub(psub(pmk(CELL(CF_Q + v, q), CELL(CF_Q + v, q2)), pc<P>(Qi[v])), pc<P>(dl[v]));
+                dp[v] = kept ? psub(pmk(dqk[q][v], dqk[q2][v]), pc<P>(dl[v]))
+                             : psub(psub(pmk(CELL(CF_Q + v, q), CELL(CF_Q + v, q2)), pc<P>(Qi[v])), pc<P>(dl[v]));
 #pragma unroll
               for (int c = 0; c < 3; ++c) {
                 kp2[c] = pmk(CELL(CF_K + c, q), CELL(CF_K + c, q2));
@@ -794,7 +819,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
               for (int c = 0; c < 3; ++c) out[1 + c] = pfma(pm, kp2[c], pmul(dp[1 + c], U));
               out[4] = pmul(padd(dp[4], pm), U);
             }
-            const P ijp = pmk(CELL(CF_INVJ, q), CELL(CF_INVJ, q2));
+            const P ijp = kept ? pmk(ijk[q], ijk[q2]) : pmk(CELL(CF_INVJ, q), CELL(CF_INVJ, q2));
             const P ds = pmk(d5[s], -d5[s]);
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
