@@ -701,11 +701,12 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         const T knr = Num<T>::rsqrt_(kf[0] * kf[0] + kf[1] * kf[1] + kf[2] * kf[2]);
         const T n[3] = {kf[0] * knr, kf[1] * knr, kf[2] * knr};
         // first tangent, normalised: e_z x n where n is far from e_z, else n x e_x.  Chosen by
-        // selects (faster for linear upwind and WENO7), except in the folded WENO5 sweep, where
-        // the selects cost registers and a branch measured faster.
+        // selects (faster for linear upwind, WENO7 and component-wise WENO5), except in the
+        // folded WENO5 sweep, where the selects cost registers, and in WENOCU6: there a branch
+        // measured faster.
         T t1[3], t2[3];
         const bool lowz = n[2] * n[2] <= T(0.5);
-        if constexpr (SCHEME == 0 && FIX == 1) {
+        if constexpr ((SCHEME == 0 && FIX == 1) || SCHEME == 3) {
           if (lowz) {
             const T s = Num<T>::rsqrt_(n[0] * n[0] + n[1] * n[1]);
             t1[0] = -n[1] * s; t1[1] = n[0] * s; t1[2] = T(0);
