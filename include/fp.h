@@ -48,7 +48,10 @@ typedef enum {
   FP_ERR_TIMEOUT = 5,      /* reserved: a bounded device-side wait gave up.  No kernel of this
                               library waits on another (work items are assigned statically and
                               no launch waits on a flag), so no call returns it at present */
-  FP_ERR_UNSUPPORTED = 6   /* valid but not implemented combination */
+  FP_ERR_UNSUPPORTED = 6,  /* valid but not implemented combination */
+  FP_ERR_BOUNDS = 7        /* bounds-checking build only (fp_bounds_checking() == 1): a kernel met
+                              an element index outside its array; the access went to the array's
+                              first element instead, so results are wrong but nothing faulted */
 } fp_status;
 
 enum { FP_WENO5_JS = 0, FP_LINEAR_UPWIND5 = 1, FP_WENO7_JS = 2, FP_WENOCU6 = 3 };
@@ -173,8 +176,17 @@ int fp_get_metrics(fp_ctx *ctx, double *host_out);
 int fp_get_face_metrics(fp_ctx *ctx, int dir, double *host_out);
 
 /* Synchronise `stream`, read and clear the device status word.  Returns FP_OK, or
-   FP_ERR_NONFINITE when an RK stage produced a non-finite state value since the last read. */
+   FP_ERR_NONFINITE when an RK stage produced a non-finite state value since the last read, or
+   (bounds-checking build) FP_ERR_BOUNDS when a kernel met an out-of-range index. */
 int fp_get_device_status(fp_ctx *ctx, void *stream);
+
+/* 1 in the bounds-checking build of the library (libfpgb300_check.so, compiled with
+   -DFPK_BOUNDS_CHECK; no counterpart in the paper), 0 in the normal build.  In the checking
+   build every global element the sweep, the halo packing and the speed and time-step
+   reductions access is checked against its array, and every shared-ring offset against the
+   ring, before the access; a violation is redirected and reported as FP_ERR_BOUNDS by
+   fp_get_device_status.  The metric kernels of fp_init_grid are not checked. */
+int fp_bounds_checking(void);
 
 /* Allocation-free residual (no counterpart in the paper; an interface of this library).
    Computes what fp_rhs computes, bit for bit, without allocating or freeing anything, for

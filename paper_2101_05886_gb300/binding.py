@@ -11,9 +11,12 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libfpgb300.so")
+# FPGB300_LIBRARY selects another build of the library, e.g. the bounds-checking build
+# libfpgb300_check.so (build.build(check=True)); it must be set before the first call.
+LIB_PATH = os.environ.get("FPGB300_LIBRARY") or os.path.join(HERE, "libfpgb300.so")
 
-FP_OK, FP_ERR_ARG, FP_ERR_CUDA, FP_ERR_OOM, FP_ERR_NONFINITE, FP_ERR_TIMEOUT, FP_ERR_UNSUPPORTED = range(7)
+(FP_OK, FP_ERR_ARG, FP_ERR_CUDA, FP_ERR_OOM, FP_ERR_NONFINITE, FP_ERR_TIMEOUT, FP_ERR_UNSUPPORTED,
+ FP_ERR_BOUNDS) = range(8)
 FP_WENO5_JS, FP_LINEAR_UPWIND5, FP_WENO7_JS, FP_WENOCU6 = 0, 1, 2, 3
 FP_F64, FP_F32_MIXED = 0, 1
 FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP, FP_BC_SLIP_WALL, FP_BC_CUT, FP_BC_BLOCK, FP_BC_HALO = 0, 1, 2, 3, 4, 5, 6
@@ -27,7 +30,7 @@ EXPORTS = [
     "fp_batch_last_error", "fp_batch_free", "fp_state_bytes", "fp_pipe_create", "fp_pipe_rk3_step_host",
     "fp_pipe_set_ordered", "fp_pipe_groups", "fp_pipe_launches_per_step", "fp_pipe_last_error", "fp_pipe_free",
     "fp_balanced_groups", "fp_debug_fail_allocation", "fp_probe_peaks", "fp_rk3_stage", "fp_set_halo",
-    "fp_halo_bytes", "fp_pack_halo",
+    "fp_halo_bytes", "fp_pack_halo", "fp_bounds_checking",
 ]
 
 
@@ -101,6 +104,7 @@ def lib():
         L.fp_balanced_groups.argtypes = [ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]
         L.fp_debug_fail_allocation.argtypes = [ctypes.c_int]
+        L.fp_bounds_checking.argtypes = []
         L.fp_probe_peaks.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3 + [_VP]
         L.fp_rk3_stage.argtypes = [_VP, _VP, ctypes.c_double, ctypes.c_int, _VP]
         L.fp_set_halo.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
@@ -331,6 +335,11 @@ def fp_balanced_groups(weights, ngroups):
 def fp_debug_fail_allocation(n):
     """Make the n-th library allocation from now fail as out of memory (n < 0: cancel)."""
     return lib().fp_debug_fail_allocation(int(n))
+
+
+def fp_bounds_checking():
+    """1 when the loaded library is the bounds-checking build, else 0."""
+    return lib().fp_bounds_checking()
 
 
 def fp_probe_peaks(stream=0):

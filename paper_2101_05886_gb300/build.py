@@ -11,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfpgb300.so")
+LIB_CHECK = os.path.join(HERE, "libfpgb300_check.so")
 SOURCES = ["api.cu", "pipe.cu", "metrics.cu", "cfl.cu", "probe.cu", "sweep_f32.cu", "sweep_f32_fix.cu", "sweep_f32_bnd.cu",
            "sweep_f32_bnd_fix.cu", "sweep_f64.cu", "sweep_f64_fix.cu", "sweep_f64_bnd.cu", "sweep_f64_bnd_fix.cu"]
 HEADERS = ["fp_internal.h", "sweep.cuh"]
@@ -34,12 +35,17 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), check: bool = False) -> str:
+    """Compile and link the library; check=True builds the bounds-checking variant
+    libfpgb300_check.so (-DFPK_BOUNDS_CHECK, objects in _build_check) beside it."""
+    bdir = BUILD + "_check" if check else BUILD
+    lib = LIB_CHECK if check else LIB
+    extra = [*extra, "-DFPK_BOUNDS_CHECK"] if check else list(extra)
+    os.makedirs(bdir, exist_ok=True)
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(bdir, src.replace(".cu", ".o"))
         if force or _stale(o, s):
             jobs.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
 
@@ -53,15 +59,15 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         rcs = list(ex.map(run, jobs))
     if any(rcs):
         raise RuntimeError("nvcc failed")
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
-    if force or jobs or not os.path.exists(LIB):
-        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    objs = [os.path.join(bdir, s.replace(".cu", ".o")) for s in SOURCES]
+    if force or jobs or not os.path.exists(lib):
+        cmd = [nvcc(), *ARCH, "-shared", "-o", lib, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True,
+    print(build(force="--force" in sys.argv, verbose=True, check="--check" in sys.argv,
                 extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))

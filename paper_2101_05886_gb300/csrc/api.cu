@@ -383,6 +383,7 @@ const char *fp_status_string(int st) {
     case FP_ERR_NONFINITE: return "non-finite state";
     case FP_ERR_TIMEOUT: return "device wait timed out";
     case FP_ERR_UNSUPPORTED: return "unsupported combination";
+    case FP_ERR_BOUNDS: return "index outside its array (bounds-checking build)";
     default: return "unknown status";
   }
 }
@@ -623,7 +624,8 @@ int fp_pack_halo(fp_ctx *c, const void *q, int stage, int dir, int side, void *o
   if (!q || !out_dev || stage < 0 || stage > 2 || dir < 0 || dir >= c->desc.dims || side < 0 || side > 1)
     return fail(c, FP_ERR_ARG, "fp_pack_halo: bad argument");
   const void *src = stage == 0 ? q : (stage == 1 ? c->q1 : c->q2);
-  cudaError_t e = fpk::launch_pack_halo(src, c->is_f32, dir, side, c->G, c->desc.n, out_dev, (cudaStream_t)stream);
+  cudaError_t e =
+      fpk::launch_pack_halo(src, c->is_f32, dir, side, c->G, c->desc.n, out_dev, c->status, (cudaStream_t)stream);
   return e == cudaSuccess ? FP_OK : cuda_fail(c, e, "fp_pack_halo");
 }
 
@@ -690,8 +692,17 @@ int fp_get_device_status(fp_ctx *c, void *stream) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "fp_get_device_status");
-  if (word & 1) return fail(c, FP_ERR_NONFINITE, "a stage produced a non-finite state");
+  if (word & fpk::ST_BOUNDS) return fail(c, FP_ERR_BOUNDS, "a kernel met an index outside its array (access redirected)");
+  if (word & fpk::ST_NONFINITE) return fail(c, FP_ERR_NONFINITE, "a stage produced a non-finite state");
   return FP_OK;
+}
+
+int fp_bounds_checking(void) {
+#ifdef FPK_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 int fp_launches_per_rhs(const fp_ctx *c) { return c ? c->desc.dims + (c->desc.global_lf ? 2 : 0) : 0; }

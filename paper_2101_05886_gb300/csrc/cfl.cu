@@ -32,12 +32,12 @@ __global__ void k_cfl(const BlockDev *blk, long long ncells, int ni, int nj, int
                  w = (double)q[3 * qc + idx] / rho;
     const double p = (g - 1.0) * ((double)q[4 * qc + idx] - 0.5 * rho * (u * u + v * v + w * w));
     const double c = sqrt(g * p / rho);
-    const double Jc = 1.0 / (double)met[9 * mc + mo];
+    const double Jc = 1.0 / (double)*FPK_IN(met + (9 * mc + mo), met, 10 * mc, blk->status);
     double s = 0.0;
     for (int d = 0; d < dims; ++d) {
-      const double gx = Jc * (double)met[(3 * d) * mc + mo];
-      const double gy = Jc * (double)met[(3 * d + 1) * mc + mo];
-      const double gz = Jc * (double)met[(3 * d + 2) * mc + mo];
+      const double gx = Jc * (double)*FPK_IN(met + ((3 * d) * mc + mo), met, 10 * mc, blk->status);
+      const double gy = Jc * (double)*FPK_IN(met + ((3 * d + 1) * mc + mo), met, 10 * mc, blk->status);
+      const double gz = Jc * (double)*FPK_IN(met + ((3 * d + 2) * mc + mo), met, 10 * mc, blk->status);
       s += fabs(u * gx + v * gy + w * gz) + c * sqrt(gx * gx + gy * gy + gz * gz);
     }
     best = s > best ? s : best;
@@ -92,10 +92,11 @@ __global__ void k_lam_max(const BlockDev *blocks, const int2 *items, int nitems,
       const T u = q[qc + idx] * rinv, v = q[2 * qc + idx] * rinv, w = q[3 * qc + idx] * rinv;
       const T p = (g - T(1)) * (q[4 * qc + idx] - T(0.5) * rho * (u * u + v * v + w * w));
       const T c = sqrt(g * p * rinv);
-      const T Jc = T(1) / met[9 * mc + mo];
+      const T Jc = T(1) / *FPK_IN(met + (9 * mc + mo), met, 10 * mc, B->status);
       for (int d = 0; d < dims; ++d) {
-        const T gx = Jc * met[(3 * d) * mc + mo], gy = Jc * met[(3 * d + 1) * mc + mo],
-                gz = Jc * met[(3 * d + 2) * mc + mo];
+        const T gx = Jc * *FPK_IN(met + ((3 * d) * mc + mo), met, 10 * mc, B->status),
+                gy = Jc * *FPK_IN(met + ((3 * d + 1) * mc + mo), met, 10 * mc, B->status),
+                gz = Jc * *FPK_IN(met + ((3 * d + 2) * mc + mo), met, 10 * mc, B->status);
         const T U = u * gx + v * gy + w * gz, a = c * sqrt(gx * gx + gy * gy + gz * gz);
         T lm = fabs(U - a), l0 = fabs(U), lp = fabs(U + a);
         if (!charwise) { lm = fmax(lm, lp); l0 = lm; lp = lm; }
@@ -121,7 +122,7 @@ __global__ void k_lam_max(const BlockDev *blocks, const int2 *items, int nitems,
 // side: cells 0..G-1; high side: cells n-G..n-1 (index x - (n - G) in the buffer).
 template <typename T>
 __global__ void k_pack_halo(const T *__restrict__ q, T *__restrict__ out, int dir, int side, int G, int ni,
-                            int nj, int nk) {
+                            int nj, int nk, int *status) {
   int e[3] = {ni, nj, nk};
   const int nd = e[dir];
   e[dir] = G;
@@ -136,14 +137,14 @@ __global__ void k_pack_halo(const T *__restrict__ q, T *__restrict__ out, int di
     c[1] = (int)(r % e[1]);
     c[2] = (int)(r / e[1]);
     c[dir] += side ? nd - G : 0;
-    out[idx] = q[v * qc + ((long long)c[2] * nj + c[1]) * ni + c[0]];
+    out[idx] = *FPK_IN(q + (v * qc + ((long long)c[2] * nj + c[1]) * ni + c[0]), q, 5 * qc, status);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_pack_halo(const void *q, int is_f32, int dir, int side, int G, const int *n, void *out,
-                             cudaStream_t s) {
+                             int *status, cudaStream_t s) {
   int e[3] = {n[0], n[1], n[2]};
   e[dir] = G;
   const long long total = 5LL * e[0] * e[1] * e[2];
@@ -152,10 +153,10 @@ cudaError_t launch_pack_halo(const void *q, int is_f32, int dir, int side, int G
   const int grid = (int)(want < 4096 ? (want < 1 ? 1 : want) : 4096);
   if (is_f32)
     k_pack_halo<float><<<grid, threads, 0, s>>>(static_cast<const float *>(q), static_cast<float *>(out), dir, side, G,
-                                                n[0], n[1], n[2]);
+                                                n[0], n[1], n[2], status);
   else
     k_pack_halo<double><<<grid, threads, 0, s>>>(static_cast<const double *>(q), static_cast<double *>(out), dir, side,
-                                                 G, n[0], n[1], n[2]);
+                                                 G, n[0], n[1], n[2], status);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,29 @@ enum : int {
 
 enum : int { MODE_WRITE = 0, MODE_ADD = 1, MODE_RHS = 2, MODE_RK = 3 };
 
+// Status word bits set by the kernels.
+enum : int { ST_NONFINITE = 1, ST_BOUNDS = 2 };
+
+// Bounds-checking builds (compiled with -DFPK_BOUNDS_CHECK, libfpgb300_check.so): before every
+// global access of the sweep, the halo packing and the speed and time-step reductions, the
+// element is checked against the array it belongs to, and every shared-ring offset against the
+// ring.  An element outside records ST_BOUNDS in the status word and the access goes to the
+// array's first element instead, so a wrong index shows as FP_ERR_BOUNDS, not as a fault.  In
+// the normal build FPK_CHK_ONLY(...) expands to nothing and FPK_IN(p, ...) to p.
+#ifdef FPK_BOUNDS_CHECK
+#define FPK_CHK_ONLY(...) __VA_ARGS__
+template <typename P>
+__device__ __forceinline__ P fpk_in(P p, P base, long long n, int *status) {
+  if (p >= base && p < base + n) return p;
+  atomicOr(status, ST_BOUNDS);
+  return base;
+}
+#define FPK_IN(p, base, n, status) ::fpk::fpk_in((p), (base), (long long)(n), (status))
+#else
+#define FPK_CHK_ONLY(...)
+#define FPK_IN(p, base, n, status) (p)
+#endif
+
 // One swept direction of one block.  A "line" runs along the swept direction; the
 // lines of a block are numbered by a flattened transverse index L = t1 + nt1 * t2.
 struct DirDev {
@@ -64,7 +87,7 @@ struct alignas(16) BlockDev {
   void *dqdt;          // output of the rhs mode
   double qbar[5];      // reference state (far-field state)
   double gamma;
-  int *status;         // device status word: bit0 non-finite state
+  int *status;         // device status word: ST_NONFINITE, ST_BOUNDS
   int global_lf;       // 1: Lax-Friedrichs speeds from lamg instead of the stencil
   void *lamg;          // T [3 directions][3]: max |U - c|grad||, |U|, |U + c|grad|| over the block
   int cut;             // FP_BC_CUT sides: lines t1 < cut or t1 >= nt1 - cut meet across the cut
@@ -139,8 +162,9 @@ cudaError_t launch_cfl(const BlockDev *blk, int is_f32, long long ncells, const 
                        unsigned long long *out_bits, cudaStream_t s);
 
 // Halo packing (cfl.cu): the G cells of stage state `stage` next to side `side` of direction
-// `dir` into `out`, in the halo layout of DirDev (the receiving block's view of them).
+// `dir` into `out`, in the halo layout of DirDev (the receiving block's view of them); `status`
+// is the context's status word (bounds-checking builds record there).
 cudaError_t launch_pack_halo(const void *q, int is_f32, int dir, int side, int G, const int *n, void *out,
-                             cudaStream_t s);
+                             int *status, cudaStream_t s);
 
 }  // namespace fpk

@@ -397,7 +397,8 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     if (tid == 0) {                      // read after the prologue's barrier
       s_dt = mode == MODE_RK ? T(*dtp) : T(0);
       if (!FIX && B->global_lf)
-        for (int c = 0; c < 3; ++c) s_lam[c] = static_cast<const T *>(B->lamg)[3 * dir + c];
+        for (int c = 0; c < 3; ++c)
+          s_lam[c] = *FPK_IN(static_cast<const T *>(B->lamg) + (3 * dir + c), static_cast<const T *>(B->lamg), 9, B->status);
     }
     const int S = D->S, TT = D->TT, W = 2 * S;
     // thread roles: along-line index tf and line index tl.  The xi pass puts
@@ -435,7 +436,13 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     const T pb = g1 * (qb[4] - T(0.5) * (qb[1] * ub[0] + qb[2] * ub[1] + qb[3] * ub[2]));
     const T mbq[3] = {qb[1], qb[2], qb[3]};
 
-    auto off = [&](int x) -> int { return lbase + (x & wm) * SS; };
+    auto off = [&](int x) -> int {
+      const int o = lbase + (x & wm) * SS;
+      FPK_CHK_ONLY(if (o < 0 || o >= kRing) { atomicOr(B->status, ST_BOUNDS); return 0; })
+      return o;
+    };
+    FPK_CHK_ONLY(const T *const metb = static_cast<const T *>(B->met);
+                 const T *const fmetb = static_cast<const T *>(D->fmet);)
 
     // boundary rule of a cell index x of this line: the source cell (its first component
     // at src, component stride cs), or the far-field state (far); `wall` asks for the
@@ -444,10 +451,12 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     // with t1 reversed, wall outside the cut width), 5 another block of the batch (its cells
     // next to its opposite side, same transverse indices, same RK stage), 6 the caller's halo
     // buffer of that side (the cells another process holds, refreshed for every RK stage).
-    auto bc_source = [&](int x, const T *&src, long long &cs, bool &far, bool &wall) {
+    auto bc_source = [&](int x, const T *&src, long long &cs, bool &far,
+                         bool &wall FPK_CHK_ONLY(, const T *&sb, long long &sn)) {
       int xx = x;
       long long qsrc = qbase;
       cs = qc; far = false; wall = false;
+      FPK_CHK_ONLY(sb = qin; sn = 5 * qc;)
       if (x < 0 || x >= nd) {
         const int bc = x < 0 ? bclo : bchi;
         if (bc == 0) { xx = x % nd; if (xx < 0) xx += nd; }
@@ -457,6 +466,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           const long long hx = x < 0 ? (long long)(x + G) : (long long)(x - nd);
           src = static_cast<const T *>(D->halo[x < 0 ? 0 : 1]) + t1 * D->hT1 + t2 * D->hT2 + hx * D->hsd;
           cs = D->hc;
+          FPK_CHK_ONLY(sb = static_cast<const T *>(D->halo[x < 0 ? 0 : 1]); sn = 5 * D->hc;)
           return;
         } else if (bc == 5) {   // rare path: the line's (t1, t2) are recovered from its offset
           const BlockDev *NB = blocks + B->nbr[dir][x < 0 ? 0 : 1];
@@ -465,6 +475,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           src = static_cast<const T *>(NB->q[stage]) + s1 * ND->qT1 + s2 * ND->qT2 +
                 (long long)(x < 0 ? ND->nd + x : x - nd) * ND->qsd;
           cs = NB->qc;
+          FPK_CHK_ONLY(sb = static_cast<const T *>(NB->q[stage]); sn = 5 * NB->qc;)
           return;
         } else {
           xx = x < 0 ? -1 - x : 2 * nd - 1 - x;
@@ -483,20 +494,22 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
       if (x >= -G && x < nd + G) {
         const long long mo = (long long)x * msd;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) k[a] = met[(3LL * dir + a) * mc + mo];
-        invJ = met[9LL * mc + mo];
+        for (int a = 0; a < 3; ++a) k[a] = *FPK_IN(met + ((3LL * dir + a) * mc + mo), metb, 10 * mc, B->status);
+        invJ = *FPK_IN(met + (9LL * mc + mo), metb, 10 * mc, B->status);
         const T *qp;
         long long cs;
         bool far, wall;
-        bc_source(x, qp, cs, far, wall);
+        FPK_CHK_ONLY(const T *sb; long long sn;)
+        bc_source(x, qp, cs, far, wall FPK_CHK_ONLY(, sb, sn));
         if (far) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) Q[v] = qb[v];
         } else {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) Q[v] = __ldg(qp + v * cs);
+          for (int v = 0; v < 5; ++v) Q[v] = __ldg(FPK_IN(qp + v * cs, sb, sn, B->status));
           // slip wall: reflect about the boundary face of this line (face -1/2 or nd-1/2)
-          if (BND && wall) wall_reflect<T>(Q, fmet + (x < 0 ? 0LL : (long long)nd * fsd), fcs);
+          if (BND && wall)
+            wall_reflect<T>(Q, FPK_IN(fmet + (x < 0 ? 0LL : (long long)nd * fsd), fmetb, fcs, B->status), fcs);
         }
       } else {   // beyond every stencil that a face of this line uses
 #pragma unroll
@@ -536,25 +549,28 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     auto prefetch_face = [&](int ff, int slot) {
       T *dst = nsb + tid + (9 + 3 * slot) * kThreads;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) cp_async_el(dst + c * kThreads, fmet + c * fcs + (long long)(ff + 1) * fsd);
+      for (int c = 0; c < 3; ++c)
+        cp_async_el(dst + c * kThreads, FPK_IN(fmet + c * fcs + (long long)(ff + 1) * fsd, fmetb, 3 * fcs, B->status));
     };
     auto prefetch_cell = [&](int x) {
       T *dst = nsb + tid;
       if (x >= -G && x < nd + G) {
         const long long mo = (long long)x * msd;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) cp_async_el(dst + (5 + a) * kThreads, met + (3LL * dir + a) * mc + mo);
-        cp_async_el(dst + 8 * kThreads, met + 9LL * mc + mo);
+        for (int a = 0; a < 3; ++a)
+          cp_async_el(dst + (5 + a) * kThreads, FPK_IN(met + (3LL * dir + a) * mc + mo, metb, 10 * mc, B->status));
+        cp_async_el(dst + 8 * kThreads, FPK_IN(met + 9LL * mc + mo, metb, 10 * mc, B->status));
         const T *qp;
         long long cs;
         bool far, wall;
-        bc_source(x, qp, cs, far, wall);
+        FPK_CHK_ONLY(const T *sb; long long sn;)
+        bc_source(x, qp, cs, far, wall FPK_CHK_ONLY(, sb, sn));
         if (far) {
 #pragma unroll
           for (int v = 0; v < 5; ++v) dst[v * kThreads] = qb[v];
         } else {   // a wall ghost copies its mirror cell; the reflection is applied when staged
 #pragma unroll
-          for (int v = 0; v < 5; ++v) cp_async_el(dst + v * kThreads, qp + v * cs);
+          for (int v = 0; v < 5; ++v) cp_async_el(dst + v * kThreads, FPK_IN(qp + v * cs, sb, sn, B->status));
         }
       } else {
 #pragma unroll
@@ -573,17 +589,20 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
       if (mode != MODE_WRITE) {
         const T *ra = static_cast<const T *>(B->racc) + qo;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) cp_async_el(dst + v * kThreads, ra + v * qc);
+        for (int v = 0; v < 5; ++v)
+          cp_async_el(dst + v * kThreads, FPK_IN(ra + v * qc, static_cast<const T *>(B->racc), 5 * qc, B->status));
       }
       if (mode == MODE_RK && stage != 0) {
         const T *qn = static_cast<const T *>(B->q[0]) + qo;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) cp_async_el(dst + (5 + v) * kThreads, qn + v * qc);
+        for (int v = 0; v < 5; ++v)
+          cp_async_el(dst + (5 + v) * kThreads, FPK_IN(qn + v * qc, static_cast<const T *>(B->q[0]), 5 * qc, B->status));
       }
       if (fpform) {
         const T *dkp = static_cast<const T *>(D->dk) + qo;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) cp_async_el(dst + (10 + c) * kThreads, dkp + c * qc);
+        for (int c = 0; c < 3; ++c)
+          cp_async_el(dst + (10 + c) * kThreads, FPK_IN(dkp + c * qc, static_cast<const T *>(D->dk), 3 * qc, B->status));
       }
     };
 
@@ -995,19 +1014,21 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           for (int v = 0; v < 5; ++v) R[v] += t1v[v] + t2v[v];
         }
         T *racc = static_cast<T *>(B->racc) + qo;
+        FPK_CHK_ONLY(T *const raccb = static_cast<T *>(B->racc);)
         const T *ra = epb + tid;                      // prefetched accumulator
         if (mode == MODE_WRITE) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) racc[v * qc] = R[v];
+          for (int v = 0; v < 5; ++v) *FPK_IN(racc + v * qc, raccb, 5 * qc, B->status) = R[v];
         } else if (mode == MODE_ADD) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) racc[v * qc] = ra[v * kThreads] + R[v];
+          for (int v = 0; v < 5; ++v) *FPK_IN(racc + v * qc, raccb, 5 * qc, B->status) = ra[v * kThreads] + R[v];
         } else {
           const T Jc = Num<T>::rcp(sm[CF_INVJ * kRing + ox]);
           if (mode == MODE_RHS) {
             T *out = static_cast<T *>(B->dqdt) + qo;
 #pragma unroll
-            for (int v = 0; v < 5; ++v) out[v * qc] = -Jc * (ra[v * kThreads] + R[v]);
+            for (int v = 0; v < 5; ++v)
+              *FPK_IN(out + v * qc, static_cast<T *>(B->dqdt), 5 * qc, B->status) = -Jc * (ra[v * kThreads] + R[v]);
           } else {
             // SSP-RK3 stage (Gottlieb & Shu) in increment form:
             // Q^(s+1) = Q^(s) + a_s (Q^n - Q^(s)) + b_s dt L(Q^(s))
@@ -1022,10 +1043,10 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
               const T Lv = -Jc * (ra[v * kThreads] + R[v]);
               T nv = qk + bs * dt * Lv;
               if (stage != 0) nv = qk + as * (ra[(5 + v) * kThreads] - qk) + bs * dt * Lv;
-              qo_p[v * qc] = nv;
+              *FPK_IN(qo_p + v * qc, static_cast<T *>(B->q[(stage + 1) % 3]), 5 * qc, B->status) = nv;
               bad |= !isfinite(nv);
             }
-            if (bad) atomicOr(B->status, 1);
+            if (bad) atomicOr(B->status, ST_NONFINITE);
           }
         }
       }
@@ -1040,8 +1061,9 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           const T *qp;
           long long cs;
           bool far, wall;
-          bc_source(xs, qp, cs, far, wall);
-          if (wall) wall_reflect<T>(Q, fmet + (long long)nd * fsd, fcs);
+          FPK_CHK_ONLY(const T *sb; long long sn;)
+          bc_source(xs, qp, cs, far, wall FPK_CHK_ONLY(, sb, sn));
+          if (wall) wall_reflect<T>(Q, FPK_IN(fmet + (long long)nd * fsd, fmetb, fcs, B->status), fcs);
         }
         stage_cell(xs, Q, k, src[8 * kThreads]);
       }

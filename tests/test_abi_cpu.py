@@ -38,8 +38,13 @@ def test_ghost_widths(lib):
 
 
 def test_status_strings(lib):
-    for st in range(7):
-        assert lib.fp_status_string(st)
+    for st in range(8):
+        assert lib.fp_status_string(st) != b"unknown status"
+    assert lib.fp_status_string(8) == b"unknown status"
+
+
+def test_the_normal_build_does_not_check_bounds():
+    assert B.fp_bounds_checking() == 0
 
 
 @pytest.mark.parametrize("field,value", [("dims", 4), ("metric_order", 5), ("scheme", 4), ("precision", 3),
