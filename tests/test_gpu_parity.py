@@ -874,14 +874,16 @@ def test_ordered_pipe_sees_host_states_written_by_earlier_stream_work():
 
 
 # ---- full-size parity in the benchmark's launch configuration ----
-def test_full_size_batched_workload_sampled_parity():
+@pytest.mark.parametrize("scheme", [B.FP_WENO5_JS, B.FP_LINEAR_UPWIND5])
+def test_full_size_batched_workload_sampled_parity(scheme):
     """The 64-block batched workload at full size (34.5M points) with the benchmark's autotuned
     tiles and persistent launches (the residual call runs one launch per pass over all blocks;
     the timed graph runs the same kernel over two halves of the blocks, equal per block bit for
     bit, see the batch tests): dQ/dt of sampled blocks against the oracle on interior
     sub-boxes next to the low corner, in the middle and next to the high corner.  FP32 on a
     Mach 3 stream with a 1e-3 perturbation (float-rounded state and q_inf on both sides):
-    within 1e-5 of the parity metric."""
+    within 1e-5 of the parity metric.  Both schemes the benchmark times on this workload:
+    WENO5-JS and linear upwind."""
     M = 6
     Gn = O.node_ghost(M)
     qinf = f32(I.uniform_qinf(3.0, 0.0))
@@ -893,7 +895,7 @@ def test_full_size_batched_workload_sampled_parity():
         g = (I.cylinder_ogrid(n, Lz=float(rng.uniform(1.0, 8.0)), Gn=Gn) if k < 32
              else I.periodic_wavy_3d(n, L=10.0, amp=0.08, Gn=Gn))
         q = f32(I.perturbed_state(g, qinf, amp=1e-3, seed=k))
-        blk = Block(g, metric_order=M, precision=F32, q_inf=qinf)
+        blk = Block(g, metric_order=M, scheme=scheme, precision=F32, q_inf=qinf)
         states.append(blk.to_device(q))
         blocks.append(blk)
         if k in sample:
@@ -907,7 +909,7 @@ def test_full_size_batched_workload_sampled_parity():
         n = np.array(sizes[k])
         for lo in (np.array([G, G, G]), (n - 6) // 2, n - 6 - G):
             got = outs[k][:, lo[2]:lo[2] + 6, lo[1]:lo[1] + 6, lo[0]:lo[0] + 6].cpu().numpy()
-            err = subbox_err(got, g, q, M, lo, np.array((6, 6, 6)), qinf=qinf)
+            err = subbox_err(got, g, q, M, lo, np.array((6, 6, 6)), qinf=qinf, scheme=scheme)
             assert err <= 1e-5, (k, lo, err)
     bat.close()
     for b in blocks:
