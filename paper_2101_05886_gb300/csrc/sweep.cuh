@@ -649,32 +649,38 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         for (int c = 0; c < 3; ++c) kf[c] = nsb[(9 + 3 * (ch & 1) + c) * kThreads + tid];
 
         // reference face state Q* = Q_i + delta (Eqs. Q_star, QdJ_star, 1dJ at order M)
+        using P = typename PairOf<T>::type;
         T dl[5] = {T(0), T(0), T(0), T(0), T(0)};
-        // linear upwind with the switches folded keeps the cells' Q_q - Q_i and (1/J)_q of this
-        // loop for its stencil differences instead of loading them again (M6: 36 shared loads)
+        // The cells q = kQlo .. kQlo + M - 1 of the weighted sum are taken in mirror pairs
+        // (kQlo + m, kQlo + M - 1 - m), m < M/2, whose weights are equal, two cells per packed
+        // instruction.  These are the stencil loops' pairs (q, 7 - q) of the same cells, so linear
+        // upwind with the switches folded keeps the pairs' Q_q - Q_i and (1/J)_q for its stencil
+        // differences instead of loading and subtracting them again.
         constexpr bool kKeep = SCHEME == 1 && FIX == 1;
-        constexpr int kQlo = 3 - M / 2 + 1, kQhi = kQlo + M;     // cells q of the weighted sum
-        T dqk[8][5], ijk[8];
+        constexpr int kQlo = 3 - M / 2 + 1;
+        P dqk[4][5], ijk[4];
         if (fpform) {
-          T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
-          T wsum = T(0);
+          P acc[5];
 #pragma unroll
-          for (int m = 0; m < M; ++m) {
-            const int q = kQlo + m;
-            const T ij = CELL(CF_INVJ, q);
-            const T w = T(MidW<M>::w(m)) * ij;
-            wsum += w;
-            if (kKeep) ijk[q] = ij;
+          for (int v = 0; v < 5; ++v) acc[v] = pc<P>(T(0));
+          P wsum = pc<P>(T(0));
+#pragma unroll
+          for (int m = 0; m < M / 2; ++m) {
+            const int q = kQlo + m, q2 = kQlo + M - 1 - m;
+            const P ij = pmk(CELL(CF_INVJ, q), CELL(CF_INVJ, q2));
+            const P w = pmul(pc<P>(T(MidW<M>::w(m))), ij);
+            wsum = padd(wsum, w);
+            if (kKeep) ijk[m] = ij;
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
-              const T dq = CELL(CF_Q + v, q) - Qi[v];
-              if (kKeep) dqk[q][v] = dq;
-              acc[v] += w * dq;
+              const P dq = psub(pmk(CELL(CF_Q + v, q), CELL(CF_Q + v, q2)), pc<P>(Qi[v]));
+              if (kKeep) dqk[m][v] = dq;
+              acc[v] = pfma(w, dq, acc[v]);
             }
           }
-          const T wi = Num<T>::rcp(wsum);
+          const T wi = Num<T>::rcp(wsum.x + wsum.y);
 #pragma unroll
-          for (int v = 0; v < 5; ++v) dl[v] = acc[v] * wi;
+          for (int v = 0; v < 5; ++v) dl[v] = (acc[v].x + acc[v].y) * wi;
         }
         T Qs[5];
 #pragma unroll
@@ -751,7 +757,6 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         const T h2[3] = {T(0.5) * t2[0], T(0.5) * t2[1], T(0.5) * t2[2]};
         const T hut1 = T(0.5) * ut1, hut2 = T(0.5) * ut2;
 
-        using P = typename PairOf<T>::type;
         // (1/2) l_s . d for the five characteristic fields
         auto project = [&](const T d[5], T c[5]) {
           if (!charwise) {
@@ -807,13 +812,15 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
           for (int s = 0; s < 3; ++s) {
             const int q = s + 1, q2 = 6 - s;
             P dp[5], out[5];
-            // both cells among those of the weighted sum (all of them at M6)
-            const bool kept = kKeep && q >= kQlo && q2 < kQhi;
+            // the weighted sum's pair of these two cells, if it has one (every pair at M6 and M8)
+            const int km = q - kQlo;
+            const bool kept = kKeep && km >= 0;
+            const int kmi = kept ? km : 0;
             if (fpform) {
               P kp2[3], uBp[3];
 #pragma unroll
               for (int v = 0; v < 5; ++v)
-                dp[v] = kept ? psub(pmk(dqk[q][v], dqk[q2][v]), pc<P>(dl[v]))
+                dp[v] = kept ? psub(dqk[kmi][v], pc<P>(dl[v]))
                              : psub(psub(pmk(CELL(CF_Q + v, q), CELL(CF_Q + v, q2)), pc<P>(Qi[v])), pc<P>(dl[v]));
 #pragma unroll
               for (int c = 0; c < 3; ++c) {
@@ -839,7 +846,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
               for (int c = 0; c < 3; ++c) out[1 + c] = pfma(pm, kp2[c], pmul(dp[1 + c], U));
               out[4] = pmul(padd(dp[4], pm), U);
             }
-            const P ijp = kept ? pmk(ijk[q], ijk[q2]) : pmk(CELL(CF_INVJ, q), CELL(CF_INVJ, q2));
+            const P ijp = kept ? ijk[kmi] : pmk(CELL(CF_INVJ, q), CELL(CF_INVJ, q2));
             const P ds = pmk(d5[s], -d5[s]);
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
