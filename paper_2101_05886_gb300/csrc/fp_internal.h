@@ -103,8 +103,8 @@ struct SweepLaunch {
   int stage;           // RK stage 0,1,2 (input q[stage], output q[(stage+1)%3])
   const double *dt;    // device scalar
   int grid;            // CTAs of the persistent launch
-  int bnd;             // some block of the launch has a slip-wall or cut side in `dir`
-  int glf;             // the blocks of the launch use global Lax-Friedrichs speeds
+  int bnd = 0;         // some block of the launch has a slip-wall or cut side in `dir`
+  int glf = 0;         // the blocks of the launch use global Lax-Friedrichs speeds
 };
 
 // Launchers of the sweep, one per translation unit (sweep_<NAME>.cu): precision f32 / f64,
