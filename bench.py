@@ -55,7 +55,7 @@ BYTES_PER_CELL_STAGE_F64 = 2 * BYTES_PER_CELL_STAGE_F32
 ALG_FLOPS_PER_POINT_PASS = {"weno5_char": 2000.0, "lu5_char": 700.0}
 # FP32 operations the kernels execute per point and pass, counted by ncu on the 16-block
 # subset (FFMA 2, FFMA2 4, FADD/FMUL 1, FADD2/FMUL2 2): reported beside the algorithmic count.
-EXEC_FLOPS_PER_POINT_PASS = {"weno5_char": 2167.0, "lu5_char": 1096.0}
+EXEC_FLOPS_PER_POINT_PASS = {"weno5_char": 2143.0, "lu5_char": 1130.0}
 # DRAM bytes per point per direction pass measured by ncu (16-block capture, mean over an RK
 # step: 96.4 B), scaled to a pass over the workload.  The linear-upwind sweep makes the same
 # loads and stores (78.0 / 99.4 / 100.8 B per point in its captured passes against 77.9 /
