@@ -65,12 +65,25 @@ class LocalHalo:
 
 
 class DistHalo:
-    """Halo exchange between processes through torch.distributed point-to-point messages."""
+    """Halo exchange between processes through torch.distributed point-to-point messages.
 
-    def __init__(self, backend, neighbours, rank):
+    staging="host" moves the messages through page-locked host buffers (for a transport that
+    takes no device buffers, such as gloo, with device slabs): the packed cells are copied to
+    the host before the exchange and the received ones back to the device halos after it, on
+    the current stream, so the next stage sees them."""
+
+    def __init__(self, backend, neighbours, rank, staging=None):
         self.b = backend
         self.lo, self.hi = neighbours
         self.rank = rank
+        self.staging = staging
+        if staging not in (None, "host"):
+            raise ValueError("staging is None or 'host'")
+        if staging == "host":
+            import torch
+            pin = getattr(backend, "device", "cpu") != "cpu"
+            self.hsend = [None if t is None else torch.empty(t.shape, dtype=t.dtype, pin_memory=pin) for t in backend.send]
+            self.hrecv = [None if t is None else torch.empty(t.shape, dtype=t.dtype, pin_memory=pin) for t in backend.recv]
 
     def exchange(self, q, stage):
         import torch.distributed as dist
@@ -79,22 +92,31 @@ class DistHalo:
             if b.has_halo(side):
                 b.pack(q, stage, side)
         b.sync()
+        send, recv = (self.hsend, self.hrecv) if self.staging else (b.send, b.recv)
+        if self.staging:
+            for side in (0, 1):
+                if send[side] is not None:
+                    send[side].copy_(b.send[side])        # waits for the packing
         ops = []
         # receives: low halo first (tag 0), then high halo (tag 1); a halo on side s is sent
         # by the neighbour's side 1 - s
         if self.lo is not None:
-            ops.append(dist.P2POp(dist.irecv, b.recv[0], self.lo, tag=0))
+            ops.append(dist.P2POp(dist.irecv, recv[0], self.lo, tag=0))
         if self.hi is not None:
-            ops.append(dist.P2POp(dist.irecv, b.recv[1], self.hi, tag=1))
+            ops.append(dist.P2POp(dist.irecv, recv[1], self.hi, tag=1))
         # sends: high side first (it lands in the high neighbour's low halo, tag 0)
         if self.hi is not None:
-            ops.append(dist.P2POp(dist.isend, b.send[1], self.hi, tag=0))
+            ops.append(dist.P2POp(dist.isend, send[1], self.hi, tag=0))
         if self.lo is not None:
-            ops.append(dist.P2POp(dist.isend, b.send[0], self.lo, tag=1))
+            ops.append(dist.P2POp(dist.isend, send[0], self.lo, tag=1))
         # one group of point-to-point operations (NCCL runs them together, so two ranks that
         # both receive first cannot wait on each other)
         for r in dist.batch_isend_irecv(ops) if ops else []:
             r.wait()
+        if self.staging:
+            for side in (0, 1):
+                if recv[side] is not None:
+                    b.recv_into(side, recv[side])
 
 
 class SlabStepper:
@@ -131,7 +153,8 @@ class SlabStepper:
             import torch
             import torch.distributed as dist
             if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
-                dev = self.backends[0].device
+                # NCCL reduces device tensors; gloo takes the value on the host
+                dev = "cpu" if dist.get_backend(self.group) == "gloo" else self.backends[0].device
                 t = torch.tensor([dt], dtype=torch.float64, device=dev)
                 dist.all_reduce(t, op=dist.ReduceOp.MIN, group=self.group)
                 dt = float(t.item())

@@ -82,6 +82,79 @@ def test_halo_slabs_equal_the_unsplit_block(name, precision):
         b.close()
 
 
+def _process_slab(rank, world, port, name, precision, q_out):
+    """One process, one slab on cuda:0, halos exchanged with the other process through host
+    memory over gloo (DistHalo staging="host"): its residual and two RK3 steps."""
+    import os
+
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.cuda.set_device(0)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    g, qinf, q, d, parts, M = _case(name, precision)
+    grids, nbrs, sizes = S.slab_grids(g, world, d)
+    ax = 3 - d
+    k0 = sum(sizes[:rank])
+    blk = Block(grids[rank], metric_order=M, precision=precision, q_inf=qinf)
+    sl = S.BlockSlab(blk, d)
+    mine = np.ascontiguousarray(np.take(q, np.arange(k0, k0 + sizes[rank]), axis=ax))
+    state = blk.to_device(mine)
+    stepper = S.SlabStepper([sl], S.DistHalo(sl, nbrs[rank], rank, staging="host"), [state])
+    rhs = stepper.rhs([torch.empty_like(state)])[0].cpu().numpy()
+    dt = stepper.cfl_dt(0.5) * 0.5
+    for _ in range(2):
+        stepper.rk3_step(dt)
+    torch.cuda.synchronize()
+    q_out.put((rank, rhs, state.cpu().numpy(), dt, blk.status()))
+    dist.barrier()
+    blk.close()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("name,precision", [("wavy_k3", F64), ("wavy_k3", F32)])
+def test_two_processes_with_host_staged_halos_equal_the_unsplit_block(name, precision):
+    """The slab decomposition as it runs across processes (one slab per process, the halo cells
+    packed on the device, exchanged between the processes before every RK stage, the time step
+    reduced over them), here with two processes that share this GPU and exchange through host
+    memory over gloo.  No kernel of one process waits on the other's; the processes meet on the
+    host between stages.  Their residual and two RK3 steps equal the unsplit block's."""
+    import socket
+
+    import torch.multiprocessing as mp
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q_out = ctx.Queue()
+    procs = [ctx.Process(target=_process_slab, args=(r, 2, port, name, precision, q_out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted([q_out.get(timeout=600) for _ in range(2)], key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert all(r[4] == B.FP_OK for r in res)
+    assert res[0][3] == res[1][3]                      # one time step for both processes
+    g, qinf, q, d, parts, M = _case(name, precision)
+    ax = 3 - d
+    whole = Block(g, metric_order=M, precision=precision, q_inf=qinf)
+    qd = whole.to_device(q)
+    ref = whole.rhs(qd).cpu().numpy()
+    got = np.concatenate([r[1] for r in res], axis=ax)
+    cfg = O.cfg_for(g, M=M, qinf=qinf)
+    P = Parity(cfg, O.metrics(cfg, g.nodes, g.Gn), q)
+    assert residual_err(-got * P.invJ, -ref * P.invJ, P.tau) <= (1e-14 if precision == F64 else 1e-6)
+    dt = res[0][3]
+    for _ in range(2):
+        whole.rk3_step(qd, dt)
+    torch.cuda.synchronize()
+    stepped = np.concatenate([r[2] for r in res], axis=ax)
+    assert state_err(stepped - q, qd.cpu().numpy() - q) <= (1e-13 if precision == F64 else 1e-5)
+    whole.close()
+
+
 def test_halo_blocks_refuse_calls_that_cannot_refresh_their_halos():
     g, qinf, q, d, parts, M = _case("wavy_k3", F64)
     grids, nbrs, sizes = S.slab_grids(g, parts, d)

@@ -59,6 +59,9 @@ class OracleSlab:
     def sync(self):
         pass
 
+    def recv_into(self, side, src):
+        self.recv[side].copy_(src)
+
     def _L(self, qs):
         ext = np.concatenate([self.recv[0].numpy(), qs, self.recv[1].numpy()], axis=1)
         _, dq = self.O.rhs(self.cfg, self.met, ext)
@@ -82,7 +85,7 @@ class OracleSlab:
         return self.O.cfl_dt(self.cfg_own, self.met_own, q.numpy(), cfl)
 
 
-def _worker(rank, world, port, q_out):
+def _worker(rank, world, port, q_out, staging=None):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -95,7 +98,7 @@ def _worker(rank, world, port, q_out):
     q_full = I.vortex_3d(full, mach=0.8, eps=5.0, L=10.0)
     q = torch.from_numpy(np.ascontiguousarray(q_full[:, k0:k0 + sizes[rank]]))
     b = OracleSlab(k0, k0 + sizes[rank], qinf)
-    stepper = S.SlabStepper([b], S.DistHalo(b, nbrs[rank], rank), [q])
+    stepper = S.SlabStepper([b], S.DistHalo(b, nbrs[rank], rank, staging=staging), [q])
     dt = 0.5 * stepper.cfl_dt(0.5)
     rhs = stepper.rhs([torch.empty_like(q)])[0].numpy().copy()
     for _ in range(2):
@@ -105,13 +108,16 @@ def _worker(rank, world, port, q_out):
     dist.destroy_process_group()
 
 
-def test_two_rank_slab_steps_equal_the_unsplit_oracle():
+@pytest.mark.parametrize("staging", [None, "host"])
+def test_two_rank_slab_steps_equal_the_unsplit_oracle(staging):
+    """The messages go straight between the ranks' halo buffers, or (staging="host") through
+    separate host buffers, as for device slabs over a host transport."""
     import oracle as O
     from paper_2101_05886_gb300 import inputs as I
     ctx = mp.get_context("spawn")
     q_out = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q_out)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q_out, staging)) for r in range(2)]
     for p in procs:
         p.start()
     res = sorted([q_out.get(timeout=300) for _ in range(2)], key=lambda r: r[0])
