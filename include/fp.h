@@ -230,7 +230,9 @@ size_t fp_state_bytes(const fp_ctx *ctx);
 int fp_launches_per_rhs(const fp_ctx *ctx);
 int fp_launches_per_step(const fp_ctx *ctx);
 
-/* Tile shape used for direction dir: faces per chunk and lines per tile. */
+/* Tile shape used for direction dir: faces per chunk and lines per tile.  Defaults: 32 x 8
+   along xi; 8 x 32 along eta and zeta, or 32 x 8 there when 8 x 32 would give fewer work
+   items than the device holds resident CTAs (small blocks).  Results do not depend on it. */
 int fp_get_tile(const fp_ctx *ctx, int dir, int *faces, int *lines);
 /* Override the tile shape (faces in {8,16,32}, faces*lines == 256). */
 int fp_set_tile(fp_ctx *ctx, int dir, int faces, int lines);

@@ -504,6 +504,13 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
   fill_dirs(c);
   c->per_sm = prepare(c->is_f32, M, desc->scheme);
   FP_TRY(cudaGetLastError(), "prepare sweep kernels");
+  // a block too small to fill the resident CTAs with the default tiles of the eta and zeta
+  // passes (32 lines x 8 faces) takes 8 lines x 32 faces there: four times the work items,
+  // each a quarter as long (batches pick their tiles by timing them instead)
+  for (int d = 1; d < c->desc.dims; ++d) {
+    DirDev &D = c->hblk.dir[d];
+    if ((D.nlines + D.TT - 1) / D.TT < (long long)c->per_sm * c->nsm) { D.S = 32; D.TT = 8; }
+  }
   int st = upload_items(c);
   if (st != FP_OK) { fp_free(c); return st; }
 #undef FP_TRY
