@@ -160,7 +160,9 @@ def test_cfl_dt_parity():
 
 @pytest.mark.parametrize("name,M,scheme,charwise", [("2d_vortex", 6, 0, 1), ("3d_vortex", 6, 0, 1), ("3d_vortex", 2, 1, 1),
                                                     ("3d_ogrid", 6, 0, 1), ("3d_vortex", 6, 1, 1), ("3d_ogrid", 6, 1, 1),
-                                                    ("3d_vortex", 6, 1, 0), ("2d_config1", 6, 1, 1)])
+                                                    ("3d_vortex", 6, 1, 0), ("2d_config1", 6, 1, 1),
+                                                    ("3d_vortex", 8, 0, 1), ("3d_ogrid", 4, 0, 1), ("3d_min", 6, 0, 1),
+                                                    ("3d_min", 8, 1, 1), ("2d_vortex", 4, 1, 1)])
 def test_rhs_parity_fp32_mixed(name, M, scheme, charwise):
     g, qinf, q = _case(name, M)
     q32, qinf = f32(q), f32(qinf)     # the same (float-representable) inputs on both sides
