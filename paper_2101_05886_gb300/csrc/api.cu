@@ -44,6 +44,8 @@ struct fp_ctx {
   int nitems[3] = {0, 0, 0};
   int per_sm = 1;
   int nsm = 152;
+  int nt = fpk::kThreads;   // threads of the sweep variant's CTA (faces per chunk x lines per tile)
+  int pad = 1;              // its xi rings padded (every tile shape conflict-free) or not (S = 32 only)
   int dev = 0;                        // the device the context's memory lives on
   double dt_host = 0.0;
   std::string err;
@@ -70,6 +72,7 @@ struct fp_batch {
   int2 *bitems[kMaxBranch][3] = {};
   int bnitems[kMaxBranch][3] = {};
   int per_sm = 1, nsm = 152;
+  int nt = fpk::kThreads, pad = 1;   // the blocks' sweep CTA shape (all blocks share it)
   int2 *lam_items = nullptr;
   int nlam_items = 0;
   std::string err;
@@ -190,22 +193,29 @@ int has_halo(const fp_grid_desc &d) {
 
 int ghost_of(int M, int scheme) { return std::max(scheme == FP_WENO7_JS ? 4 : 3, M / 2); }
 
-// resident CTAs per SM of the sweep (the fewest over its variants), after opting every
-// variant in to its dynamic shared memory
-int prepare(int is_f32, int M, int scheme) {
+// resident CTAs per SM of the sweep variants a context runs (folded switches or not; the fewer
+// of the plain and the boundary-rule instantiation), after opting every variant in to its
+// dynamic shared memory
+int prepare(int is_f32, int M, int scheme, int fix) {
   using P = int (*)(int, int);
   const P f32[4] = {fpk::prepare_sweep_f32, fpk::prepare_sweep_f32_fix, fpk::prepare_sweep_f32_bnd,
                     fpk::prepare_sweep_f32_bnd_fix};
   const P f64[4] = {fpk::prepare_sweep_f64, fpk::prepare_sweep_f64_fix, fpk::prepare_sweep_f64_bnd,
                     fpk::prepare_sweep_f64_bnd_fix};
-  int nb = 1 << 20;
-  for (P p : is_f32 ? f32 : f64) nb = std::min(nb, p(M, scheme));
-  return nb;
+  const P *p = is_f32 ? f32 : f64;
+  int nb[4];
+  for (int v = 0; v < 4; ++v) nb[v] = p[v](M, scheme);
+  return std::min(nb[fix], nb[2 + fix]);
+}
+
+// the switches are folded for characteristic FP sweeps with local speeds (not for WENOCU6,
+// whose sweep measured 1 % slower with them folded)
+int fix_of(int scheme, int charwise, int fp, int global_lf) {
+  return charwise && fp && !global_lf && scheme != FP_WENOCU6 ? 1 : 0;
 }
 
 // the variant of the launch: boundary rules compiled in when some block of the launch has such a
-// side in its direction, the switches folded for characteristic FP sweeps with local speeds (not
-// for WENOCU6, whose sweep measured 1 % slower with them folded)
+// side in its direction, the switches folded as fix_of says
 cudaError_t launch(int is_f32, const fpk::SweepLaunch &L, int M, int scheme, int charwise, int fp,
                    cudaStream_t s) {
   using F = cudaError_t (*)(const fpk::SweepLaunch &, int, int, int, int, cudaStream_t);
@@ -213,14 +223,15 @@ cudaError_t launch(int is_f32, const fpk::SweepLaunch &L, int M, int scheme, int
                     fpk::launch_sweep_f32_bnd_fix};
   const F f64[4] = {fpk::launch_sweep_f64, fpk::launch_sweep_f64_fix, fpk::launch_sweep_f64_bnd,
                     fpk::launch_sweep_f64_bnd_fix};
-  const int v = (L.bnd ? 2 : 0) + (charwise && fp && !L.glf && scheme != FP_WENOCU6 ? 1 : 0);
+  const int v = (L.bnd ? 2 : 0) + fix_of(scheme, charwise, fp, L.glf);
   return (is_f32 ? f32 : f64)[v](L, M, scheme, charwise, fp, s);
 }
 
-void default_tile(int dir, int nd, int *S, int *TT) {
-  (void)nd;
-  if (dir == 0) { *S = 32; *TT = 8; }
-  else { *S = 8; *TT = 32; }
+// default tile of a direction for a CTA of nt threads: 32 faces along xi, 8 across lines
+// elsewhere (32 lines of 8 faces at 256 threads)
+void default_tile(int dir, int nt, int *S, int *TT) {
+  *S = dir == 0 ? 32 : 8;
+  *TT = nt / *S;
 }
 
 void fill_dirs(fp_ctx *c) {
@@ -274,8 +285,8 @@ void fill_dirs(fp_ctx *c) {
       D.hT2 = st[tb];
       D.hc = e[0] * e[1] * e[2];
     }
-    if (d < dims) default_tile(d, D.nd, &D.S, &D.TT);
-    else { D.S = 8; D.TT = 32; D.nlines = 0; }
+    if (d < dims) default_tile(d, c->nt, &D.S, &D.TT);
+    else { default_tile(d, c->nt, &D.S, &D.TT); D.nlines = 0; }
   }
   B.dims = dims;
   B.G = G;
@@ -501,15 +512,20 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
     FP_TRY(cudaMemcpy(c->lam_items, li.data(), li.size() * sizeof(int2), cudaMemcpyHostToDevice),
            "copy speed items");
   }
-  fill_dirs(c);
-  c->per_sm = prepare(c->is_f32, M, desc->scheme);
+  {
+    const int fix = fix_of(desc->scheme, desc->characteristic, desc->free_stream_preserving, desc->global_lf);
+    c->nt = fpk::sweep_threads(c->is_f32, desc->scheme, fix);
+    c->pad = fpk::sweep_padded(c->is_f32, desc->scheme, fix) ? 1 : 0;
+    fill_dirs(c);
+    c->per_sm = prepare(c->is_f32, M, desc->scheme, fix);
+  }
   FP_TRY(cudaGetLastError(), "prepare sweep kernels");
   // a block too small to fill the resident CTAs with the default tiles of the eta and zeta
-  // passes (32 lines x 8 faces) takes 8 lines x 32 faces there: four times the work items,
+  // passes (8 faces per chunk) takes 32 faces per chunk there: four times the work items,
   // each a quarter as long (batches pick their tiles by timing them instead)
   for (int d = 1; d < c->desc.dims; ++d) {
     DirDev &D = c->hblk.dir[d];
-    if ((D.nlines + D.TT - 1) / D.TT < (long long)c->per_sm * c->nsm) { D.S = 32; D.TT = 8; }
+    if ((D.nlines + D.TT - 1) / D.TT < (long long)c->per_sm * c->nsm) { D.S = 32; D.TT = c->nt / 32; }
   }
   int st = upload_items(c);
   if (st != FP_OK) { fp_free(c); return st; }
@@ -725,8 +741,11 @@ int fp_get_tile(const fp_ctx *c, int dir, int *faces, int *lines) {
 int fp_set_tile(fp_ctx *c, int dir, int faces, int lines) {
   if (!c) return FP_ERR_ARG;
   if (dir < 0 || dir >= c->desc.dims) return fail(c, FP_ERR_ARG, "fp_set_tile: bad direction");
-  if (!(faces == 8 || faces == 16 || faces == 32) || faces * lines != fpk::kThreads)
-    return fail(c, FP_ERR_ARG, "fp_set_tile: faces in {8,16,32} and faces*lines == 256");
+  if (!(faces == 8 || faces == 16 || faces == 32) || faces * lines != c->nt)
+    return fail(c, FP_ERR_ARG, "fp_set_tile: faces in {8,16,32} and faces*lines == the sweep's CTA size "
+                               "(the product of fp_get_tile's shape)");
+  if (dir == 0 && !c->pad && faces != 32)
+    return fail(c, FP_ERR_ARG, "fp_set_tile: this sweep's xi rings are unpadded: 32 faces per chunk only");
   c->hblk.dir[dir].S = faces;
   c->hblk.dir[dir].TT = lines;
   return upload_items(c);
@@ -825,7 +844,7 @@ static int batch_pass(fp_batch *b, int d, int mode, int stage, cudaStream_t s) {
 // Autotuner: for each direction and each line-length class, time every tile shape
 // on the blocks of that class and keep the fastest.
 static int batch_autotune(fp_batch *b, cudaStream_t s) {
-  static const int cand[3][2] = {{32, 8}, {16, 16}, {8, 32}};
+  const int cand[3][2] = {{32, b->nt / 32}, {16, b->nt / 16}, {8, b->nt / 8}};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -842,6 +861,7 @@ static int batch_autotune(fp_batch *b, cudaStream_t s) {
       float best = 1e30f;
       int bestc = 0;
       for (int ci = 0; ci < 3; ++ci) {
+        if (d == 0 && !b->pad && cand[ci][0] != 32) continue;   // unpadded xi rings: S = 32 only
         for (int k : members) { b->hblk[k].dir[d].S = cand[ci][0]; b->hblk[k].dir[d].TT = cand[ci][1]; }
         int st = batch_upload(b, s);
         if (!st) st = batch_items(b, d, &members);
@@ -910,6 +930,8 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
   b->is_f32 = d0.precision == FP_F32_MIXED;
   b->global_lf = d0.global_lf;
   b->per_sm = blocks[0]->per_sm;
+  b->nt = blocks[0]->nt;
+  b->pad = blocks[0]->pad;
   b->nsm = blocks[0]->nsm;
   for (int k = 0; k < nblocks; ++k) {
     b->ctx.push_back(blocks[k]);

@@ -7,12 +7,32 @@
 
 namespace fpk {
 
-constexpr int kThreads = 256;        // threads per sweep CTA (faces per chunk x lines per tile)
+constexpr int kThreads = 256;        // threads of a sweep CTA unless sweep_threads says otherwise
 constexpr int kCellFields = 17;      // per-cell values staged in shared memory
 constexpr int kFaceFields = 10;      // per-face values staged in shared memory (W, delta)
 constexpr int kNextFields = 15;      // staged per thread: next chunk's cell (Q, k, 1/J), face metrics x2
 constexpr int kEpiFields = 13;       // epilogue operands staged per thread (accumulator, Q^n, dk)
 constexpr int kRing = 3 * kThreads;  // shared-memory stride of one staged field (2S slots x TT lines, padded)
+
+// CTA shape of a sweep variant (precision, scheme, switches folded or not): its threads, which
+// equal faces per chunk x lines per tile, whether the rings of the xi pass (lines of 2S
+// slots, one after the other) are padded to 3S slots per line so that every tile shape is
+// free of bank conflicts (unpadded, the xi pass takes S = 32 only), and the CTAs one SM holds.
+// The folded FP32 WENO5 and linear-upwind sweeps run 128-thread CTAs: the same 16 warps per SM
+// as two 256-thread CTAs in four independent groups (WENO5), or 20 warps at 96 registers with
+// unpadded rings (linear upwind).
+__host__ __device__ constexpr int sweep_threads(bool f32, int scheme, int fix) {
+  return (f32 && fix && (scheme == 0 || scheme == 1)) ? 128 : kThreads;
+}
+__host__ __device__ constexpr bool sweep_padded(bool f32, int scheme, int fix) {
+  return !(f32 && fix && scheme == 1);
+}
+__host__ __device__ constexpr int sweep_ring(bool f32, int scheme, int fix) {
+  return (sweep_padded(f32, scheme, fix) ? 3 : 2) * sweep_threads(f32, scheme, fix);
+}
+__host__ __device__ constexpr int sweep_min_ctas(bool f32, int scheme, int fix) {
+  return !f32 || scheme == 2 ? 1 : (sweep_threads(f32, scheme, fix) == kThreads ? 2 : (scheme == 1 ? 5 : 4));
+}
 
 // Shared-memory field indices of a staged cell.
 enum : int {
@@ -63,7 +83,7 @@ struct DirDev {
   long long fT1, fT2, fsd;  // face-metric offsets, face f+1/2 at (f+1)*fsd
   long long fc;        // face-metric component stride
   int bclo, bchi;      // boundary codes at the two line ends
-  int S, TT;           // faces per chunk, lines per tile (S * TT == kThreads)
+  int S, TT;           // faces per chunk, lines per tile (S * TT == the variant's sweep_threads)
   const void *fmet;    // T [3][faces]
   const void *dk;      // T [3][cells]: k_{i+1/2} - k_{i-1/2} along this direction (FP64-formed)
   // FP_BC_HALO sides: the caller's buffers of the G cells beyond each side, laid out like the

@@ -347,9 +347,13 @@ __device__ __forceinline__ void dflux_pair(T g1, typename PairOf<T>::type rinvB,
 // all fixed at compile time (the configuration of the paper's workloads but the shock test), so
 // their switches fold away; FIX = 0 reads them from the arguments and the block descriptor.
 template <typename T, int M, int SCHEME, bool BND, int FIX>
-__global__ void __launch_bounds__(kThreads, (sizeof(T) == 4 && SCHEME != 2 ? 2 : 1))
+__global__ void __launch_bounds__(sweep_threads(sizeof(T) == 4, SCHEME, FIX), sweep_min_ctas(sizeof(T) == 4, SCHEME, FIX))
 fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, int nitems, int dir,
          int mode, int stage, const double *__restrict__ dtp, int charwise_arg, int fpform_arg) {
+  // this variant's CTA shape (fp_internal.h): threads, ring stride of a staged field, padding
+  constexpr int kThreads = sweep_threads(sizeof(T) == 4, SCHEME, FIX);
+  constexpr int kRing = sweep_ring(sizeof(T) == 4, SCHEME, FIX);
+  constexpr bool kPad = sweep_padded(sizeof(T) == 4, SCHEME, FIX);
   const int charwise = FIX ? 1 : charwise_arg;
   const int fpform = FIX ? 1 : fpform_arg;
   // stencil points of a face: i-2..i+3 (5th order) or i-3..i+4 (WENO7), offset index Q0
@@ -358,8 +362,8 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
   extern __shared__ __align__(16) unsigned char smraw[];
   T *const sm = reinterpret_cast<T *>(smraw);              // cell ring: kCellFields x kRing
   T *const fr = sm + kCellFields * kRing;                   // face ring: kFaceFields x kRing
-  T *const nsb = fr + kFaceFields * kRing;                  // next chunk's cell, per thread: 9 x 256
-  T *const epb = nsb + kNextFields * kThreads;              // epilogue operands, per thread: 16 x 256
+  T *const nsb = fr + kFaceFields * kRing;                  // next chunk's cell and face metrics, per thread
+  T *const epb = nsb + kNextFields * kThreads;              // epilogue operands, per thread
   const int tid = threadIdx.x;
   // Work-item descriptors in shared memory, double-buffered: during an item's first chunk
   // the next item's (block, first line) and its whole block descriptor are copied in with
@@ -404,11 +408,12 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
     // thread roles: along-line index tf and line index tl.  The xi pass puts
     // consecutive threads along the line (coalesced, i contiguous), the other passes
     // across lines.  Shared layout: slot-fast lines are 3S apart (conflict-free for
-    // S < 32 as well), line-fast slots are TT apart.
+    // S < 32 as well) or, unpadded, 2S apart (the host then gives the xi pass S = 32),
+    // line-fast slots are TT apart.
     const bool slotFast = (dir == 0);
     const int tf = slotFast ? (tid % S) : (tid / TT);
     const int tl = slotFast ? (tid / S) : (tid % TT);
-    const int LS = slotFast ? 3 * S : 1;
+    const int LS = slotFast ? (kPad ? 3 : 2) * S : 1;
     const int SS = slotFast ? 1 : TT;
     const int lbase = tl * LS;
     const int wm = W - 1;
@@ -1079,12 +1084,20 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
   }
 }
 
+// dynamic shared memory of a sweep variant: the cell and face rings, then the per-thread slots
+template <typename T, int SCHEME, int FIX>
+constexpr size_t sweep_smem() {
+  return ((size_t)(kCellFields + kFaceFields) * sweep_ring(sizeof(T) == 4, SCHEME, FIX) +
+          (size_t)(kNextFields + kEpiFields) * sweep_threads(sizeof(T) == 4, SCHEME, FIX)) * sizeof(T);
+}
+
 template <typename T, int M, int SCHEME, bool BND, int FIX>
 cudaError_t launch_one(const SweepLaunch &L, int charwise, int fp, cudaStream_t s) {
-  const size_t smem = ((size_t)(kCellFields + kFaceFields) * kRing + (size_t)(kNextFields + kEpiFields) * kThreads) * sizeof(T);
+  constexpr size_t smem = sweep_smem<T, SCHEME, FIX>();
+  constexpr int nt = sweep_threads(sizeof(T) == 4, SCHEME, FIX);
   if (L.nitems <= 0) return cudaSuccess;
-  fp_sweep<T, M, SCHEME, BND, FIX><<<L.grid, kThreads, smem, s>>>(L.blocks, L.items, L.nitems, L.dir, L.mode,
-                                                           L.stage, L.dt, charwise, fp);
+  fp_sweep<T, M, SCHEME, BND, FIX><<<L.grid, nt, smem, s>>>(L.blocks, L.items, L.nitems, L.dir, L.mode,
+                                                            L.stage, L.dt, charwise, fp);
   return cudaGetLastError();
 }
 
@@ -1105,14 +1118,15 @@ cudaError_t launch_sweep_t(const SweepLaunch &L, int M, int scheme, int charwise
 // CTAs per SM of the requested one.  Called before any launch or graph capture.
 template <typename T, bool BND, int FIX>
 int prepare_t(int M, int scheme) {
-  const size_t smem = ((size_t)(kCellFields + kFaceFields) * kRing + (size_t)(kNextFields + kEpiFields) * kThreads) * sizeof(T);
   int nb = 0;
 #define FPK_OCC(MM, SS)                                                                              \
   {                                                                                                  \
+    constexpr size_t smem = sweep_smem<T, SS, FIX>();                                                \
     cudaFuncSetAttribute(fp_sweep<T, MM, SS, BND, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                          (int)smem);                                                                 \
     if (M == MM && scheme == SS)                                                                     \
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fp_sweep<T, MM, SS, BND, FIX>, kThreads, smem); \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fp_sweep<T, MM, SS, BND, FIX>,              \
+                                                    sweep_threads(sizeof(T) == 4, SS, FIX), smem);   \
   }
   FPK_OCC(2, 0) FPK_OCC(4, 0) FPK_OCC(6, 0) FPK_OCC(8, 0)
   FPK_OCC(2, 1) FPK_OCC(4, 1) FPK_OCC(6, 1) FPK_OCC(8, 1)
