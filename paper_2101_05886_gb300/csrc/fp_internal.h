@@ -18,20 +18,22 @@ constexpr int kRing = 3 * kThreads;  // shared-memory stride of one staged field
 // equal faces per chunk x lines per tile, whether the rings of the xi pass (lines of 2S
 // slots, one after the other) are padded to 3S slots per line so that every tile shape is
 // free of bank conflicts (unpadded, the xi pass takes S = 32 only), and the CTAs one SM holds.
-// The folded FP32 WENO5 and linear-upwind sweeps run 128-thread CTAs: the same 16 warps per SM
-// as two 256-thread CTAs in four independent groups (WENO5), or 20 warps at 96 registers with
-// unpadded rings (linear upwind).
+// Small CTAs pay: the warps of a CTA meet at two barriers per chunk, so with fewer warps per
+// CTA the phases of the chunk (staging, FMA-heavy faces, epilogue) of different CTAs overlap
+// instead of running in step.  The folded FP32 WENO5 sweep runs 8 CTAs of 64 threads per SM,
+// unpadded (16 warps, 128 registers); the other FP32 sweeps 4 of 128 (WENO7, at up to 255
+// registers: 2); FP64 sweeps 2 of 128.
 __host__ __device__ constexpr int sweep_threads(bool f32, int scheme, int fix) {
-  return (f32 && fix && (scheme == 0 || scheme == 1)) ? 128 : kThreads;
+  return (f32 && fix && scheme == 0) ? 64 : 128;
 }
 __host__ __device__ constexpr bool sweep_padded(bool f32, int scheme, int fix) {
-  return !(f32 && fix && scheme == 1);
+  return !(f32 && fix && scheme == 0);
 }
 __host__ __device__ constexpr int sweep_ring(bool f32, int scheme, int fix) {
   return (sweep_padded(f32, scheme, fix) ? 3 : 2) * sweep_threads(f32, scheme, fix);
 }
 __host__ __device__ constexpr int sweep_min_ctas(bool f32, int scheme, int fix) {
-  return !f32 || scheme == 2 ? 1 : (sweep_threads(f32, scheme, fix) == kThreads ? 2 : (scheme == 1 ? 5 : 4));
+  return !f32 || scheme == 2 ? 2 : 512 / sweep_threads(f32, scheme, fix);
 }
 
 // Shared-memory field indices of a staged cell.

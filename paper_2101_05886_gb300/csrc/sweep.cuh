@@ -372,14 +372,13 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
   // keep evicting.
   static_assert(sizeof(BlockDev) % 16 == 0, "descriptor copied in 16-byte pieces");
   constexpr int kDescPieces = (int)(sizeof(BlockDev) / 16);
-  static_assert(kDescPieces <= kThreads, "one piece per thread");
   __shared__ __align__(16) unsigned char s_desc[2][sizeof(BlockDev)];
   __shared__ __align__(16) int2 s_item[2];
   __shared__ T s_dt;
   __shared__ T s_lam[3];                // global Lax-Friedrichs speeds of this item's direction
   auto fetch_desc = [&](int buf, int blk) {
-    if (tid < kDescPieces)
-      cp_async16(s_desc[buf] + 16 * tid, reinterpret_cast<const unsigned char *>(blocks + blk) + 16 * tid);
+    for (int p = tid; p < kDescPieces; p += kThreads)
+      cp_async16(s_desc[buf] + 16 * p, reinterpret_cast<const unsigned char *>(blocks + blk) + 16 * p);
   };
   if (blockIdx.x < nitems) {            // the first item's descriptor, loaded before the loop
     if (tid == 0) s_item[0] = items[blockIdx.x];
