@@ -230,11 +230,17 @@ size_t fp_state_bytes(const fp_ctx *ctx);
 int fp_launches_per_rhs(const fp_ctx *ctx);
 int fp_launches_per_step(const fp_ctx *ctx);
 
-/* Tile shape used for direction dir: faces per chunk and lines per tile.  Defaults: 32 x 8
-   along xi; 8 x 32 along eta and zeta, or 32 x 8 there when 8 x 32 would give fewer work
-   items than the device holds resident CTAs (small blocks).  Results do not depend on it. */
+/* Threads per CTA of the context's sweep (no counterpart in the paper): the primary size, and
+   an alternative one (0 if none; the folded FP32 sweeps have one, which a batch's autotuner
+   may pick per direction).  A tile has faces x lines equal to one of them. */
+int fp_get_cta_sizes(const fp_ctx *ctx, int *primary, int *alternative);
+/* Tile shape used for direction dir: faces per chunk and lines per tile.  Defaults: 32 faces
+   along xi; 8 faces along eta and zeta, or 32 there when 8 would give fewer work items than
+   the device holds resident CTAs (small blocks); lines = the primary CTA size / faces.
+   Results do not depend on it. */
 int fp_get_tile(const fp_ctx *ctx, int dir, int *faces, int *lines);
-/* Override the tile shape (faces in {8,16,32}, faces*lines == 256). */
+/* Override the tile shape: faces in {8,16,32}, faces x lines one of fp_get_cta_sizes; a size
+   whose xi rings are unpadded takes 32 faces along xi only (FP_ERR_ARG otherwise). */
 int fp_set_tile(fp_ctx *ctx, int dir, int faces, int lines);
 
 const char *fp_last_error(const fp_ctx *ctx);
@@ -277,6 +283,8 @@ int fp_batch_rk3_step(fp_batch *batch, double dt, void *stream);
 /* dqdt for every block (no graph); dqdt_devs[b] has block b's state layout. */
 int fp_batch_rhs(fp_batch *batch, void *const *dqdt_devs, void *stream);
 int fp_batch_launches_per_step(const fp_batch *batch);
+/* Tile shape the batch runs block `block` with in direction dir (after autotuning, if any). */
+int fp_batch_get_tile(const fp_batch *batch, int block, int dir, int *faces, int *lines);
 const char *fp_batch_last_error(const fp_batch *batch);
 void fp_batch_free(fp_batch *batch);       /* NULL-safe */
 

@@ -25,8 +25,8 @@ FP_BC_PERIODIC, FP_BC_FARFIELD, FP_BC_EXTRAP, FP_BC_SLIP_WALL, FP_BC_CUT, FP_BC_
 EXPORTS = [
     "fp_ghost_width", "fp_node_ghost_width", "fp_init_grid", "fp_rhs", "fp_rhs_noalloc", "fp_rk3_step", "fp_cfl_dt",
     "fp_get_metrics", "fp_get_face_metrics", "fp_get_device_status", "fp_launches_per_rhs",
-    "fp_launches_per_step", "fp_get_tile", "fp_set_tile", "fp_last_error", "fp_status_string",
-    "fp_free", "fp_batch_create", "fp_batch_create_linked", "fp_batch_rk3_step", "fp_batch_rhs", "fp_batch_launches_per_step",
+    "fp_launches_per_step", "fp_get_cta_sizes", "fp_get_tile", "fp_set_tile", "fp_last_error", "fp_status_string",
+    "fp_free", "fp_batch_create", "fp_batch_create_linked", "fp_batch_rk3_step", "fp_batch_rhs", "fp_batch_launches_per_step", "fp_batch_get_tile",
     "fp_batch_last_error", "fp_batch_free", "fp_state_bytes", "fp_pipe_create", "fp_pipe_rk3_step_host",
     "fp_pipe_set_ordered", "fp_pipe_groups", "fp_pipe_launches_per_step", "fp_pipe_last_error", "fp_pipe_free",
     "fp_balanced_groups", "fp_debug_fail_allocation", "fp_probe_peaks", "fp_rk3_stage", "fp_set_halo",
@@ -69,6 +69,7 @@ def lib():
         L.fp_get_device_status.argtypes = [_VP, _VP]
         L.fp_launches_per_rhs.argtypes = [_VP]
         L.fp_launches_per_step.argtypes = [_VP]
+        L.fp_get_cta_sizes.argtypes = [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.fp_get_tile.argtypes = [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.fp_set_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.fp_last_error.argtypes = [_VP]
@@ -85,6 +86,8 @@ def lib():
         L.fp_batch_rk3_step.argtypes = [_VP, ctypes.c_double, _VP]
         L.fp_batch_rhs.argtypes = [_VP, ctypes.POINTER(_VP), _VP]
         L.fp_batch_launches_per_step.argtypes = [_VP]
+        L.fp_batch_get_tile.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]
         L.fp_batch_last_error.argtypes = [_VP]
         L.fp_batch_last_error.restype = ctypes.c_char_p
         L.fp_batch_free.argtypes = [_VP]
@@ -224,6 +227,13 @@ def fp_launches_per_step(ctx):
     return lib().fp_launches_per_step(ctx)
 
 
+def fp_get_cta_sizes(ctx):
+    """(primary, alternative) threads per CTA of the context's sweep; alternative 0 if none."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(lib().fp_get_cta_sizes(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
+
+
 def fp_get_tile(ctx, direction):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(lib().fp_get_tile(ctx, direction, ctypes.byref(a), ctypes.byref(b)), ctx)
@@ -275,6 +285,15 @@ def fp_batch_rhs(batch, dqdt_ptrs, stream=0):
 
 def fp_batch_launches_per_step(batch):
     return lib().fp_batch_launches_per_step(batch)
+
+
+def fp_batch_get_tile(batch, block, direction):
+    """(faces, lines) the batch runs block `block` with in `direction`."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    st = lib().fp_batch_get_tile(batch, int(block), int(direction), ctypes.byref(a), ctypes.byref(b))
+    if st != FP_OK:
+        raise FPError(st, "fp_batch_get_tile")
+    return a.value, b.value
 
 
 def fp_batch_free(batch):

@@ -12,8 +12,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfpgb300.so")
 LIB_CHECK = os.path.join(HERE, "libfpgb300_check.so")
-SOURCES = ["api.cu", "pipe.cu", "metrics.cu", "cfl.cu", "probe.cu", "sweep_f32.cu", "sweep_f32_fix.cu", "sweep_f32_bnd.cu",
-           "sweep_f32_bnd_fix.cu", "sweep_f64.cu", "sweep_f64_fix.cu", "sweep_f64_bnd.cu", "sweep_f64_bnd_fix.cu"]
+SOURCES = ["api.cu", "pipe.cu", "metrics.cu", "cfl.cu", "probe.cu", "sweep_f32.cu", "sweep_f32_fix.cu", "sweep_f32_fix2.cu",
+           "sweep_f32_bnd.cu", "sweep_f32_bnd_fix.cu", "sweep_f32_bnd_fix2.cu", "sweep_f64.cu", "sweep_f64_fix.cu",
+           "sweep_f64_bnd.cu", "sweep_f64_bnd_fix.cu"]
 HEADERS = ["fp_internal.h", "sweep.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -42,10 +42,12 @@ struct fp_ctx {
   std::vector<int2> hitems[3];
   int2 *items[3] = {nullptr, nullptr, nullptr};
   int nitems[3] = {0, 0, 0};
-  int per_sm = 1;
   int nsm = 152;
-  int nt = fpk::kThreads;   // threads of the sweep variant's CTA (faces per chunk x lines per tile)
-  int pad = 1;              // its xi rings padded (every tile shape conflict-free) or not (S = 32 only)
+  // CTA shapes of the context's sweep: [0] the primary one, [1] the alternative (nshape == 2,
+  // the folded FP32 sweeps): threads (faces per chunk x lines per tile), xi rings padded (every
+  // tile shape conflict-free) or not (S = 32 only), resident CTAs per SM
+  int nshape = 1;
+  int nt[2] = {128, 128}, pad[2] = {1, 1}, per_sm[2] = {1, 1};
   int dev = 0;                        // the device the context's memory lives on
   double dt_host = 0.0;
   std::string err;
@@ -71,8 +73,9 @@ struct fp_batch {
   int nbranch = 1;
   int2 *bitems[kMaxBranch][3] = {};
   int bnitems[kMaxBranch][3] = {};
-  int per_sm = 1, nsm = 152;
-  int nt = fpk::kThreads, pad = 1;   // the blocks' sweep CTA shape (all blocks share it)
+  int nsm = 152;
+  int nshape = 1, nt[2] = {128, 128}, pad[2] = {1, 1}, per_sm[2] = {1, 1};   // as fp_ctx (shared by all blocks)
+  int shape = 0;                     // the one CTA shape the batch runs (sweep_batch_shape)
   int2 *lam_items = nullptr;
   int nlam_items = 0;
   std::string err;
@@ -198,14 +201,34 @@ int ghost_of(int M, int scheme) { return std::max(scheme == FP_WENO7_JS ? 4 : 3,
 // dynamic shared memory
 int prepare(int is_f32, int M, int scheme, int fix) {
   using P = int (*)(int, int);
-  const P f32[4] = {fpk::prepare_sweep_f32, fpk::prepare_sweep_f32_fix, fpk::prepare_sweep_f32_bnd,
-                    fpk::prepare_sweep_f32_bnd_fix};
-  const P f64[4] = {fpk::prepare_sweep_f64, fpk::prepare_sweep_f64_fix, fpk::prepare_sweep_f64_bnd,
-                    fpk::prepare_sweep_f64_bnd_fix};
+  const P f32[6] = {fpk::prepare_sweep_f32, fpk::prepare_sweep_f32_fix, fpk::prepare_sweep_f32_fix2,
+                    fpk::prepare_sweep_f32_bnd, fpk::prepare_sweep_f32_bnd_fix, fpk::prepare_sweep_f32_bnd_fix2};
+  const P f64[6] = {fpk::prepare_sweep_f64, fpk::prepare_sweep_f64_fix, nullptr,
+                    fpk::prepare_sweep_f64_bnd, fpk::prepare_sweep_f64_bnd_fix, nullptr};
   const P *p = is_f32 ? f32 : f64;
-  int nb[4];
-  for (int v = 0; v < 4; ++v) nb[v] = p[v](M, scheme);
-  return std::min(nb[fix], nb[2 + fix]);
+  int nb[6] = {1 << 20, 1 << 20, 1 << 20, 1 << 20, 1 << 20, 1 << 20};
+  for (int v = 0; v < 6; ++v)
+    if (p[v]) nb[v] = p[v](M, scheme);
+  return std::min(nb[fix], nb[3 + fix]);
+}
+
+// the CTA shapes of a sweep (fp_internal.h sweep_threads) and their resident CTAs per SM
+template <typename C>
+void set_shapes(C *c, int is_f32, int M, int scheme, int fix) {
+  c->nshape = fpk::sweep_has_alt(is_f32, scheme, fix) ? 2 : 1;
+  for (int a = 0; a < c->nshape; ++a) {
+    const int f = fix + a;   // fix = 2: the alternative shape
+    c->nt[a] = fpk::sweep_threads(is_f32, scheme, f);
+    c->pad[a] = fpk::sweep_padded(is_f32, scheme, f) ? 1 : 0;
+    c->per_sm[a] = prepare(is_f32, M, scheme, f);
+  }
+  if (c->nshape == 1) { c->nt[1] = c->nt[0]; c->pad[1] = c->pad[0]; c->per_sm[1] = c->per_sm[0]; }
+}
+
+// the shape (0 primary, 1 alternative) of a direction's tile
+template <typename C>
+int shape_of(const C *c, const fpk::DirDev &D) {
+  return c->nshape == 2 && D.S * D.TT == c->nt[1] ? 1 : 0;
 }
 
 // the switches are folded for characteristic FP sweeps with local speeds (not for WENOCU6,
@@ -223,8 +246,10 @@ cudaError_t launch(int is_f32, const fpk::SweepLaunch &L, int M, int scheme, int
                     fpk::launch_sweep_f32_bnd_fix};
   const F f64[4] = {fpk::launch_sweep_f64, fpk::launch_sweep_f64_fix, fpk::launch_sweep_f64_bnd,
                     fpk::launch_sweep_f64_bnd_fix};
-  const int v = (L.bnd ? 2 : 0) + fix_of(scheme, charwise, fp, L.glf);
-  return (is_f32 ? f32 : f64)[v](L, M, scheme, charwise, fp, s);
+  const int fix = fix_of(scheme, charwise, fp, L.glf);
+  if (is_f32 && fix && L.alt)
+    return (L.bnd ? fpk::launch_sweep_f32_bnd_fix2 : fpk::launch_sweep_f32_fix2)(L, M, scheme, charwise, fp, s);
+  return (is_f32 ? f32 : f64)[(L.bnd ? 2 : 0) + fix](L, M, scheme, charwise, fp, s);
 }
 
 // default tile of a direction for a CTA of nt threads: 32 faces along xi, 8 across lines
@@ -285,8 +310,8 @@ void fill_dirs(fp_ctx *c) {
       D.hT2 = st[tb];
       D.hc = e[0] * e[1] * e[2];
     }
-    if (d < dims) default_tile(d, c->nt, &D.S, &D.TT);
-    else { default_tile(d, c->nt, &D.S, &D.TT); D.nlines = 0; }
+    default_tile(d, c->nt[0], &D.S, &D.TT);
+    if (d >= dims) D.nlines = 0;
   }
   B.dims = dims;
   B.G = G;
@@ -514,10 +539,8 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
   }
   {
     const int fix = fix_of(desc->scheme, desc->characteristic, desc->free_stream_preserving, desc->global_lf);
-    c->nt = fpk::sweep_threads(c->is_f32, desc->scheme, fix);
-    c->pad = fpk::sweep_padded(c->is_f32, desc->scheme, fix) ? 1 : 0;
+    set_shapes(c, c->is_f32, M, desc->scheme, fix);
     fill_dirs(c);
-    c->per_sm = prepare(c->is_f32, M, desc->scheme, fix);
   }
   FP_TRY(cudaGetLastError(), "prepare sweep kernels");
   // a block too small to fill the resident CTAs with the default tiles of the eta and zeta
@@ -525,7 +548,7 @@ int fp_init_grid(const fp_grid_desc *desc, const double *xyz, int ghost_nodes, v
   // each a quarter as long (batches pick their tiles by timing them instead)
   for (int d = 1; d < c->desc.dims; ++d) {
     DirDev &D = c->hblk.dir[d];
-    if ((D.nlines + D.TT - 1) / D.TT < (long long)c->per_sm * c->nsm) { D.S = 32; D.TT = c->nt / 32; }
+    if ((D.nlines + D.TT - 1) / D.TT < (long long)c->per_sm[0] * c->nsm) { D.S = 32; D.TT = c->nt[0] / 32; }
   }
   int st = upload_items(c);
   if (st != FP_OK) { fp_free(c); return st; }
@@ -552,7 +575,8 @@ static int run_stage(fp_ctx *c, int stage, int rk, cudaStream_t s) {
     L.mode = d == 0 ? fpk::MODE_WRITE : (d == dims - 1 ? (rk ? fpk::MODE_RK : fpk::MODE_RHS) : fpk::MODE_ADD);
     L.stage = stage;
     L.dt = c->dt_dev;
-    L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
+    L.alt = shape_of(c, c->hblk.dir[d]);
+    L.grid = grid_for(c->per_sm[L.alt], c->nsm, L.nitems);
     L.bnd = has_bnd(c->desc, d);
     L.glf = c->desc.global_lf;
     cudaError_t e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic,
@@ -731,6 +755,13 @@ int fp_bounds_checking(void) {
 int fp_launches_per_rhs(const fp_ctx *c) { return c ? c->desc.dims + (c->desc.global_lf ? 2 : 0) : 0; }
 int fp_launches_per_step(const fp_ctx *c) { return c ? 3 * fp_launches_per_rhs(c) : 0; }
 
+int fp_get_cta_sizes(const fp_ctx *c, int *primary, int *alternative) {
+  if (!c || !primary || !alternative) return FP_ERR_ARG;
+  *primary = c->nt[0];
+  *alternative = c->nshape == 2 ? c->nt[1] : 0;
+  return FP_OK;
+}
+
 int fp_get_tile(const fp_ctx *c, int dir, int *faces, int *lines) {
   if (!c || dir < 0 || dir > 2 || !faces || !lines) return FP_ERR_ARG;
   *faces = c->hblk.dir[dir].S;
@@ -741,11 +772,12 @@ int fp_get_tile(const fp_ctx *c, int dir, int *faces, int *lines) {
 int fp_set_tile(fp_ctx *c, int dir, int faces, int lines) {
   if (!c) return FP_ERR_ARG;
   if (dir < 0 || dir >= c->desc.dims) return fail(c, FP_ERR_ARG, "fp_set_tile: bad direction");
-  if (!(faces == 8 || faces == 16 || faces == 32) || faces * lines != c->nt)
-    return fail(c, FP_ERR_ARG, "fp_set_tile: faces in {8,16,32} and faces*lines == the sweep's CTA size "
-                               "(the product of fp_get_tile's shape)");
-  if (dir == 0 && !c->pad && faces != 32)
-    return fail(c, FP_ERR_ARG, "fp_set_tile: this sweep's xi rings are unpadded: 32 faces per chunk only");
+  const int a = c->nshape == 2 && faces * lines == c->nt[1] ? 1 : 0;
+  if (!(faces == 8 || faces == 16 || faces == 32) || faces * lines != c->nt[a])
+    return fail(c, FP_ERR_ARG, "fp_set_tile: faces in {8,16,32} and faces*lines one of the sweep's CTA sizes "
+                               "(fp_get_cta_sizes)");
+  if (dir == 0 && !c->pad[a] && faces != 32)
+    return fail(c, FP_ERR_ARG, "fp_set_tile: this CTA size's xi rings are unpadded: 32 faces per chunk only");
   c->hblk.dir[dir].S = faces;
   c->hblk.dir[dir].TT = lines;
   return upload_items(c);
@@ -770,6 +802,13 @@ void fp_batch_free(fp_batch *b) {
 }
 
 const char *fp_batch_last_error(const fp_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+int fp_batch_get_tile(const fp_batch *b, int block, int dir, int *faces, int *lines) {
+  if (!b || block < 0 || block >= (int)b->hblk.size() || dir < 0 || dir > 2 || !faces || !lines) return FP_ERR_ARG;
+  *faces = b->hblk[block].dir[dir].S;
+  *lines = b->hblk[block].dir[dir].TT;
+  return FP_OK;
+}
 
 int fp_batch_launches_per_step(const fp_batch *b) {
   return b ? b->nbranch * 3 * (b->dims + (b->global_lf ? 2 : 0)) : 0;
@@ -829,7 +868,8 @@ static int batch_pass_items(fp_batch *b, int d, int mode, int stage, cudaStream_
   L.mode = mode;
   L.stage = stage;
   L.dt = b->dt_dev;
-  L.grid = grid_for(b->per_sm, b->nsm, L.nitems);
+  L.alt = shape_of(b, b->hblk[0].dir[d]);   // every block of a batch pass has the same shape
+  L.grid = grid_for(b->per_sm[L.alt], b->nsm, L.nitems);
   L.bnd = b->bnd[d];
   L.glf = b->global_lf;
   cudaError_t e = launch(b->is_f32, L, b->M, b->scheme, b->charwise, b->fp, s);
@@ -841,48 +881,62 @@ static int batch_pass(fp_batch *b, int d, int mode, int stage, cudaStream_t s) {
   return batch_pass_items(b, d, mode, stage, s, b->items[d], b->nitems[d]);
 }
 
-// Autotuner: for each direction and each line-length class, time every tile shape
-// on the blocks of that class and keep the fastest.
-static int batch_autotune(fp_batch *b, cudaStream_t s) {
-  const int cand[3][2] = {{32, b->nt / 32}, {16, b->nt / 16}, {8, b->nt / 8}};
+// Autotuner: for the batch's CTA shape, each direction and each line-length class, time every
+// tile of that shape on the blocks of that class and keep the best (tiles[a][d][k]: block k's
+// faces per chunk in direction d).
+static int batch_autotune(fp_batch *b, cudaStream_t s, std::vector<int> tiles[2][3]) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int d = 0; d < b->dims; ++d) {
-    const int nclass = 3;
-    for (int cl = 0; cl < nclass; ++cl) {
-      std::vector<int> members;
+  constexpr int nclass = 3;
+  int st = FP_OK;
+  for (int a = b->shape; a == b->shape && !st; ++a)
+    for (int d = 0; d < 3 && !st; ++d) {
+      tiles[a][d].assign(b->hblk.size(), 32);
+      if (d >= b->dims) continue;
+      std::vector<int> members[nclass];
       for (size_t k = 0; k < b->hblk.size(); ++k) {
-        int nd = b->hblk[k].dir[d].nd;
-        int c = nd < 64 ? 0 : (nd < 96 ? 1 : 2);
-        if (c == cl) members.push_back((int)k);
+        const int nd = b->hblk[k].dir[d].nd;
+        members[nd < 64 ? 0 : (nd < 96 ? 1 : 2)].push_back((int)k);
       }
-      if (members.empty()) continue;
-      float best = 1e30f;
-      int bestc = 0;
-      for (int ci = 0; ci < 3; ++ci) {
-        if (d == 0 && !b->pad && cand[ci][0] != 32) continue;   // unpadded xi rings: S = 32 only
-        for (int k : members) { b->hblk[k].dir[d].S = cand[ci][0]; b->hblk[k].dir[d].TT = cand[ci][1]; }
-        int st = batch_upload(b, s);
-        if (!st) st = batch_items(b, d, &members);
-        if (st) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
-        batch_pass(b, d, fpk::MODE_WRITE, 0, s);           // warm-up
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < 3; ++r) batch_pass(b, d, fpk::MODE_WRITE, 0, s);
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; bestc = ci; }
+      for (auto &B : b->hblk) { B.dir[d].S = 32; B.dir[d].TT = b->nt[a] / 32; }   // the pass's shape: a
+      for (int cl = 0; cl < nclass && !st; ++cl) {
+        if (members[cl].empty()) continue;
+        float best = 1e30f;
+        int bestS = 32;
+        for (int S : {32, 16, 8}) {
+          if (d == 0 && !b->pad[a] && S != 32) continue;   // unpadded xi rings: S = 32 only
+          for (int k : members[cl]) { b->hblk[k].dir[d].S = S; b->hblk[k].dir[d].TT = b->nt[a] / S; }
+          st = batch_upload(b, s);
+          if (!st) st = batch_items(b, d, &members[cl]);
+          if (!st) st = batch_pass(b, d, fpk::MODE_WRITE, 0, s);           // warm-up
+          if (st) break;
+          cudaEventRecord(e0, s);
+          for (int r = 0; r < 3; ++r) batch_pass(b, d, fpk::MODE_WRITE, 0, s);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best) { best = ms; bestS = S; }
+        }
+        for (int k : members[cl]) tiles[a][d][k] = bestS;
       }
-      for (int k : members) { b->hblk[k].dir[d].S = cand[bestc][0]; b->hblk[k].dir[d].TT = cand[bestc][1]; }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (st) return st;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return bfail(b, FP_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
   return FP_OK;
+}
+
+// the tiles of shape a from the autotuner's table
+static void batch_set_tiles(fp_batch *b, int a, std::vector<int> tiles[2][3]) {
+  for (int d = 0; d < b->dims; ++d)
+    for (size_t k = 0; k < b->hblk.size(); ++k) {
+      b->hblk[k].dir[d].S = tiles[a][d][k];
+      b->hblk[k].dir[d].TT = b->nt[a] / tiles[a][d][k];
+    }
 }
 
 int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int autotune,
@@ -929,9 +983,13 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
   b->charwise = d0.characteristic; b->fp = d0.free_stream_preserving;
   b->is_f32 = d0.precision == FP_F32_MIXED;
   b->global_lf = d0.global_lf;
-  b->per_sm = blocks[0]->per_sm;
-  b->nt = blocks[0]->nt;
-  b->pad = blocks[0]->pad;
+  b->nshape = blocks[0]->nshape;
+  for (int a = 0; a < 2; ++a) {
+    b->nt[a] = blocks[0]->nt[a];
+    b->pad[a] = blocks[0]->pad[a];
+    b->per_sm[a] = blocks[0]->per_sm[a];
+  }
+  b->shape = fpk::sweep_batch_shape(b->is_f32, b->scheme, fix_of(b->scheme, b->charwise, b->fp, b->global_lf));
   b->nsm = blocks[0]->nsm;
   for (int k = 0; k < nblocks; ++k) {
     b->ctx.push_back(blocks[k]);
@@ -943,6 +1001,11 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
       for (int sd = 0; sd < 2; ++sd) B.nbr[d][sd] = nbr[(size_t)k * 6 + d * 2 + sd];
     b->hblk.push_back(B);
   }
+  // the batch runs one CTA shape: the blocks' own tiles where they are of that shape, the
+  // defaults of that shape elsewhere
+  for (int d = 0; d < 3; ++d)
+    for (auto &B : b->hblk)
+      if (B.dir[d].S * B.dir[d].TT != b->nt[b->shape]) default_tile(d, b->nt[b->shape], &B.dir[d].S, &B.dir[d].TT);
   cudaError_t e = fpk::dev_alloc(&b->dblk, nblocks * sizeof(BlockDev));
   if (e == cudaSuccess) e = fpk::dev_alloc(&b->dt_dev, sizeof(double));
   if (e == cudaSuccess) e = fpk::host_malloc(reinterpret_cast<void **>(&b->dt_host), sizeof(double));
@@ -960,7 +1023,11 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
     if (e != cudaSuccess) { fp_batch_free(b); return e == cudaErrorMemoryAllocation ? FP_ERR_OOM : FP_ERR_CUDA; }
   }
   int st = FP_OK;
-  if (autotune) st = batch_autotune(b, s);
+  if (autotune) {
+    std::vector<int> tiles[2][3];
+    st = batch_autotune(b, s, tiles);
+    if (!st) batch_set_tiles(b, b->shape, tiles);
+  }
   if (!st) st = batch_upload(b, s);
   for (int d = 0; d < b->dims && !st; ++d) st = batch_items(b, d, nullptr);
   if (st) { std::fprintf(stderr, "fp_batch_create: %s\n", b->err.c_str()); fp_batch_free(b); return st; }
@@ -1126,7 +1193,8 @@ extern "C" int fp_rhs_noalloc(fp_ctx *c, const void *q, void *dqdt, void *stream
     L.mode = d == 0 ? fpk::MODE_WRITE : (d == dims - 1 ? fpk::MODE_RHS : fpk::MODE_ADD);
     L.stage = 0;
     L.dt = c->dt_dev;
-    L.grid = grid_for(c->per_sm, c->nsm, L.nitems);
+    L.alt = shape_of(c, c->hblk.dir[d]);
+    L.grid = grid_for(c->per_sm[L.alt], c->nsm, L.nitems);
     L.bnd = has_bnd(c->desc, d);
     L.glf = c->desc.global_lf;
     e = launch(c->is_f32, L, M, c->desc.scheme, c->desc.characteristic, c->desc.free_stream_preserving, s);

@@ -14,26 +14,43 @@ constexpr int kNextFields = 15;      // staged per thread: next chunk's cell (Q,
 constexpr int kEpiFields = 13;       // epilogue operands staged per thread (accumulator, Q^n, dk)
 constexpr int kRing = 3 * kThreads;  // shared-memory stride of one staged field (2S slots x TT lines, padded)
 
-// CTA shape of a sweep variant (precision, scheme, switches folded or not): its threads, which
-// equal faces per chunk x lines per tile, whether the rings of the xi pass (lines of 2S
-// slots, one after the other) are padded to 3S slots per line so that every tile shape is
-// free of bank conflicts (unpadded, the xi pass takes S = 32 only), and the CTAs one SM holds.
+// CTA shape of a sweep variant (precision, scheme, fix: 0 switches read at run time, 1 folded,
+// 2 folded with the alternative shape): its threads, which equal faces per chunk x lines per
+// tile, whether the rings of the xi pass (lines of 2S slots, one after the other) are padded to
+// 3S slots per line so that every tile shape is free of bank conflicts (unpadded, the xi pass
+// takes S = 32 only), and the CTAs one SM holds.
 // Small CTAs pay: the warps of a CTA meet at two barriers per chunk, so with fewer warps per
 // CTA the phases of the chunk (staging, FMA-heavy faces, epilogue) of different CTAs overlap
-// instead of running in step.  The folded FP32 WENO5 sweep runs 8 CTAs of 64 threads per SM,
-// unpadded (16 warps, 128 registers); the other FP32 sweeps 4 of 128 (WENO7, at up to 255
-// registers: 2); FP64 sweeps 2 of 128.
+// instead of running in step.  Large ones pay where the eta and zeta passes coalesce across
+// more lines (TT): a 256^3 block runs linear upwind 12 % faster at 128 threads (TT = 16) than
+// at 64 (TT = 8), a batch of blocks up to 128^3 12 % slower.  So the folded FP32 sweeps have
+// two shapes, and a batch's autotuner picks one per direction:
+//   WENO5-JS:       64 threads, unpadded, 8 CTAs per SM  |  alternative 128, padded, 4
+//   linear upwind: 128 threads, padded, 4                |  alternative  64, unpadded, 8
+//   WENO7-JS:      128 threads, padded, 2 (255 registers) |  alternative  64, unpadded, 4
+// Every other sweep: 128 threads, padded, 4 CTAs (FP32) or 2 (FP64, and WENO7).
+// Single blocks run the primary shape; batches the shape sweep_batch_shape names, which was
+// the faster one on the 64-block workload (its step graph runs two branches side by side, and
+// kernels of two shapes there would not share SMs, so a batch runs one shape throughout):
+// linear upwind the alternative (64 threads: +12 %), the others the primary.
+__host__ __device__ constexpr bool sweep_has_alt(bool f32, int scheme, int fix) {
+  return f32 && fix != 0 && scheme >= 0 && scheme <= 2;
+}
+__host__ __device__ constexpr int sweep_batch_shape(bool f32, int scheme, int fix) {
+  return sweep_has_alt(f32, scheme, fix) && scheme == 1 ? 1 : 0;
+}
 __host__ __device__ constexpr int sweep_threads(bool f32, int scheme, int fix) {
-  return (f32 && fix && scheme == 0) ? 64 : 128;
+  return !sweep_has_alt(f32, scheme, fix) ? 128
+         : ((scheme == 0) != (fix == 2) ? 64 : 128);   // WENO5 primary 64, the others' alternative 64
 }
 __host__ __device__ constexpr bool sweep_padded(bool f32, int scheme, int fix) {
-  return !(f32 && fix && scheme == 0);
+  return sweep_threads(f32, scheme, fix) != 64;
 }
 __host__ __device__ constexpr int sweep_ring(bool f32, int scheme, int fix) {
   return (sweep_padded(f32, scheme, fix) ? 3 : 2) * sweep_threads(f32, scheme, fix);
 }
 __host__ __device__ constexpr int sweep_min_ctas(bool f32, int scheme, int fix) {
-  return !f32 || scheme == 2 ? 2 : 512 / sweep_threads(f32, scheme, fix);
+  return (!f32 || scheme == 2 ? 256 : 512) / sweep_threads(f32, scheme, fix);
 }
 
 // Shared-memory field indices of a staged cell.
@@ -127,17 +144,21 @@ struct SweepLaunch {
   int grid;            // CTAs of the persistent launch
   int bnd = 0;         // some block of the launch has a slip-wall or cut side in `dir`
   int glf = 0;         // the blocks of the launch use global Lax-Friedrichs speeds
+  int alt = 0;         // the blocks' tiles in `dir` are of the alternative CTA shape
 };
 
 // Launchers of the sweep, one per translation unit (sweep_<NAME>.cu): precision f32 / f64,
 // `_bnd` with the slip-wall, cut, link and halo rules compiled in, `_fix` with the
-// characteristic decomposition and the FP form fixed on.  Each returns the cudaError_t of the
+// characteristic decomposition and the FP form fixed on, `_fix2` the same in the alternative
+// CTA shape (FP32 only).  Each returns the cudaError_t of the
 // launch; prepare_sweep_<NAME> opts in to the dynamic shared memory of its 16 (M, scheme)
 // variants and returns the resident CTAs per SM of the given one.
 cudaError_t launch_sweep_f32(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
 cudaError_t launch_sweep_f32_fix(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
 cudaError_t launch_sweep_f32_bnd(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
 cudaError_t launch_sweep_f32_bnd_fix(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
+cudaError_t launch_sweep_f32_fix2(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
+cudaError_t launch_sweep_f32_bnd_fix2(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
 cudaError_t launch_sweep_f64(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
 cudaError_t launch_sweep_f64_fix(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
 cudaError_t launch_sweep_f64_bnd(const SweepLaunch &L, int M, int scheme, int charwise, int fp, cudaStream_t s);
@@ -146,6 +167,8 @@ int prepare_sweep_f32(int M, int scheme);
 int prepare_sweep_f32_fix(int M, int scheme);
 int prepare_sweep_f32_bnd(int M, int scheme);
 int prepare_sweep_f32_bnd_fix(int M, int scheme);
+int prepare_sweep_f32_fix2(int M, int scheme);
+int prepare_sweep_f32_bnd_fix2(int M, int scheme);
 int prepare_sweep_f64(int M, int scheme);
 int prepare_sweep_f64_fix(int M, int scheme);
 int prepare_sweep_f64_bnd(int M, int scheme);

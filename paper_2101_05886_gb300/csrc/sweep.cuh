@@ -343,9 +343,10 @@ __device__ __forceinline__ void dflux_pair(T g1, typename PairOf<T>::type rinvB,
   out[4] = pfma(pc<P>(EA + pA), dU, pmul(padd(d[4], dp), UB));
 }
 
-// FIX = 1: the characteristic decomposition and the FP form on, local Lax-Friedrichs speeds,
+// FIX = 1 or 2: the characteristic decomposition and the FP form on, local Lax-Friedrichs speeds,
 // all fixed at compile time (the configuration of the paper's workloads but the shock test), so
 // their switches fold away; FIX = 0 reads them from the arguments and the block descriptor.
+// FIX = 2 is the same sweep with the alternative CTA shape of sweep_threads (fp_internal.h).
 template <typename T, int M, int SCHEME, bool BND, int FIX>
 __global__ void __launch_bounds__(sweep_threads(sizeof(T) == 4, SCHEME, FIX), sweep_min_ctas(sizeof(T) == 4, SCHEME, FIX))
 fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, int nitems, int dir,
@@ -660,7 +661,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         // instruction.  These are the stencil loops' pairs (q, 7 - q) of the same cells, so linear
         // upwind with the switches folded keeps the pairs' Q_q - Q_i and (1/J)_q for its stencil
         // differences instead of loading and subtracting them again.
-        constexpr bool kKeep = SCHEME == 1 && FIX == 1;
+        constexpr bool kKeep = SCHEME == 1 && FIX != 0;
         constexpr int kQlo = 3 - M / 2 + 1;
         P dqk[4][5], ijk[4];
         if (fpform) {
@@ -735,7 +736,7 @@ fp_sweep(const BlockDev *__restrict__ blocks, const int2 *__restrict__ items, in
         // measured faster.
         T t1[3], t2[3];
         const bool lowz = n[2] * n[2] <= T(0.5);
-        if constexpr ((SCHEME == 0 && FIX == 1) || SCHEME == 3) {
+        if constexpr ((SCHEME == 0 && FIX != 0) || SCHEME == 3) {
           if (lowz) {
             const T s = Num<T>::rsqrt_(n[0] * n[0] + n[1] * n[1]);
             t1[0] = -n[1] * s; t1[1] = n[0] * s; t1[2] = T(0);

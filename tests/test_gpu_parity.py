@@ -937,3 +937,49 @@ def test_full_size_cgrid_sampled_parity():
         err = subbox_err(got, g, q, M, lo, np.array((6, 6, 6)), qinf=qinf)
         assert err <= 1e-5, (lo, err)
     blk.close()
+
+
+# ---- CTA sizes and tile shapes ----
+@pytest.mark.parametrize("name,M,scheme,precision", [("3d_ogrid", 6, 0, F32), ("3d_ogrid", 6, 1, F32),
+                                                     ("3d_vortex", 8, 2, F32), ("3d_vortex", 6, 0, F64),
+                                                     ("ogrid_wall", 6, 0, F32), ("parabolic_cut", 6, 1, F32)])
+def test_every_tile_shape_gives_the_same_residual(name, M, scheme, precision):
+    """Every tile a context accepts (faces in {8, 16, 32}, faces x lines one of its CTA sizes;
+    32 faces along xi where that size's rings are unpadded), set direction by direction, gives
+    the residual of the default tiles bit for bit: a tile only reorders which thread computes
+    which face.  The folded FP32 sweeps have two CTA sizes (the alternative one runs other
+    kernels), including their boundary-rule variants (wall, cut); the other sweeps one."""
+    if name in ("ogrid_wall", "parabolic_cut"):
+        g, qinf, q = _wall_cut_case(name, M, scheme)
+    else:
+        g, qinf, q = _case(name, M, scheme)
+    if precision == F32:
+        q, qinf = f32(q), f32(qinf)
+    blk = Block(g, metric_order=M, scheme=scheme, precision=precision, q_inf=qinf)
+    qd = blk.to_device(q)
+    ref = blk.rhs(qd).clone()
+    primary, alternative = B.fp_get_cta_sizes(blk.ctx)
+    if precision == F32 and scheme in (0, 1, 2):
+        assert alternative in (64, 128) and alternative != primary
+    else:
+        assert alternative == 0
+    sizes = [primary] + ([alternative] if alternative else [])
+    tried = 0
+    for d in range(g.dims):
+        default = B.fp_get_tile(blk.ctx, d)
+        for nt in sizes:
+            for faces in (8, 16, 32):
+                try:
+                    B.fp_set_tile(blk.ctx, d, faces, nt // faces)
+                except B.FPError:
+                    assert d == 0 and faces != 32          # only unpadded xi rings refuse a shape
+                    continue
+                assert B.fp_get_tile(blk.ctx, d) == (faces, nt // faces)
+                assert torch.equal(blk.rhs(qd), ref), (d, faces, nt)
+                tried += 1
+        B.fp_set_tile(blk.ctx, d, *default)
+    assert tried >= g.dims * 3
+    with pytest.raises(B.FPError):
+        B.fp_set_tile(blk.ctx, 0, 32, 3)                   # not a CTA size
+    assert blk.status() == B.FP_OK
+    blk.close()
