@@ -69,7 +69,7 @@ struct fp_batch {
   // Graph branches: groups of blocks whose RK steps run as independent chains of the graph,
   // so one group's launches fill the end-of-pass tail of another's.  One branch when blocks
   // are linked (a block reads its neighbours' stage states) or the LF speeds are global.
-  static constexpr int kMaxBranch = 2;
+  static constexpr int kMaxBranch = 4;
   int nbranch = 1;
   int2 *bitems[kMaxBranch][3] = {};
   int bnitems[kMaxBranch][3] = {};
@@ -1033,8 +1033,8 @@ int fp_batch_create_linked(fp_ctx *const *blocks, int nblocks, void *const *q_de
   if (st) { std::fprintf(stderr, "fp_batch_create: %s\n", b->err.c_str()); fp_batch_free(b); return st; }
   // graph branches: blocks split into groups of about equal point count, each group's
   // items built separately
-  if (!b->global_lf && nlinks == 0 && nblocks >= fp_batch::kMaxBranch) {
-    b->nbranch = fp_batch::kMaxBranch;
+  if (!b->global_lf && nlinks == 0 && nblocks >= 2) {
+    b->nbranch = std::min(nblocks, (int)fp_batch::kMaxBranch);
     std::vector<long long> weight(nblocks);
     for (int k = 0; k < nblocks; ++k) weight[k] = blocks[k]->ncells;
     std::vector<int> group_of(nblocks);

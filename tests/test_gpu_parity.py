@@ -272,12 +272,15 @@ def test_batch_matches_single_blocks_bitwise(precision):
 
 
 def test_batch_graph_branches_and_launch_counts():
-    """An unlinked batch of two or more blocks with local LF speeds runs its RK step as two
-    graph branches (two launches per direction pass); one block, or global LF speeds (two
-    reduction launches per stage), keep one chain.  The global-LF batch step equals per-block
-    steps bit for bit."""
+    """An unlinked batch of two or more blocks with local LF speeds runs its RK step as up to
+    four graph branches (one launch per branch and direction pass); one block, or global LF
+    speeds (two reduction launches per stage), keep one chain.  The global-LF batch step
+    equals per-block steps bit for bit."""
     grids, qinf, blocks, states = _mini_batch(F32)
-    two = Batch(blocks, states, autotune=False)
+    four = Batch(blocks, states, autotune=False)
+    assert len(blocks) == 4 and four.launches_per_step() == 4 * 3 * 3
+    four.close()
+    two = Batch(blocks[:2], states[:2], autotune=False)
     assert two.launches_per_step() == 2 * 3 * 3
     two.close()
     one = Batch(blocks[:1], states[:1], autotune=False)
