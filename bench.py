@@ -55,7 +55,7 @@ BYTES_PER_CELL_STAGE_F64 = 2 * BYTES_PER_CELL_STAGE_F32
 ALG_FLOPS_PER_POINT_PASS = {"weno5_char": 2000.0, "lu5_char": 700.0}
 # FP32 operations the kernels execute per point and pass, counted by ncu on the 16-block
 # subset (FFMA 2, FFMA2 4, FADD/FMUL 1, FADD2/FMUL2 2): reported beside the algorithmic count.
-EXEC_FLOPS_PER_POINT_PASS = {"weno5_char": 2143.0, "lu5_char": 1130.0}
+EXEC_FLOPS_PER_POINT_PASS = {"weno5_char": 2145.0, "lu5_char": 1132.0}
 # DRAM bytes per point per direction pass measured by ncu (16-block capture, mean over an RK
 # step: 96.4 B), scaled to a pass over the workload.  The linear-upwind sweep makes the same
 # loads and stores (78.0 / 99.4 / 100.8 B per point in its captured passes against 77.9 /
@@ -341,7 +341,7 @@ def run_gpu(args):
     pass_ms = graph_ms / (args.steps * passes_per_step)
     full = args.blocks == 64 and world == 1
     roof = roofline("weno5_char", ncells, pass_ms, launches_per_pass, fp32_peak, peak_src, full)
-    roof["kernel"] = "fpk::fp_sweep<float,6,0,false,1> (characteristic WENO5-JS, switches folded)"
+    roof["kernel"] = "fpk::fp_sweep<float,6,0,false,1> (characteristic WENO5-JS, switches folded, 64-thread CTAs)"
 
     # ---- the FP32 residual's error against the FP64 sweep (itself within 1e-12 of the FP64
     # oracle in the parity tests), on the rank's first block at its current state
@@ -378,7 +378,7 @@ def run_gpu(args):
                "roofline": roofline("lu5_char", ncells, lpass, lbatch.launches_per_step() // passes_per_step,
                                     fp32_peak, peak_src, full),
                "finite": all(b.status() == B.FP_OK for b in lblocks)}
-        lu5["roofline"]["kernel"] = "fpk::fp_sweep<float,6,1,false,1> (characteristic linear upwind, switches folded)"
+        lu5["roofline"]["kernel"] = "fpk::fp_sweep<float,6,1,false,2> (characteristic linear upwind, switches folded, 64-thread CTAs of a batch)"
         if rank == 0:
             lu5["fp32_error_vs_fp64"] = {"max_rel": fp32_error(lblocks[0], grids[0], lstates[0],
                                                                scheme=B.FP_LINEAR_UPWIND5), "bound": 1e-5}
