@@ -883,7 +883,7 @@ def test_ordered_pipe_sees_host_states_written_by_earlier_stream_work():
 def test_full_size_batched_workload_sampled_parity(scheme):
     """The 64-block batched workload at full size (34.5M points) with the benchmark's autotuned
     tiles and persistent launches (the residual call runs one launch per pass over all blocks;
-    the timed graph runs the same kernel over two halves of the blocks, equal per block bit for
+    the timed graph runs the same kernel over up to four groups of the blocks, equal per block bit for
     bit, see the batch tests): dQ/dt of sampled blocks against the oracle on interior
     sub-boxes next to the low corner, in the middle and next to the high corner.  FP32 on a
     Mach 3 stream with a 1e-3 perturbation (float-rounded state and q_inf on both sides):
