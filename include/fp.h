@@ -257,13 +257,16 @@ void fp_free(fp_ctx *ctx);                 /* NULL-safe; synchronises the device
    A batch advances many independent blocks (same precision, scheme, metric order)
    together: one persistent launch per direction pass covers the work of every
    block, the three RK stages are captured once into a CUDA graph, and each call
-   replays it.  Unlinked batches with local Lax-Friedrichs speeds are captured as two
-   independent chains of the graph, each advancing half of the blocks (by points), so the
-   chains' launches run side by side on the GPU (then one launch per chain covers that
-   chain's blocks).  The batch keeps pointers to the contexts (they must outlive it)
-   and to the caller's state buffers q_devs[b] given at creation.  When autotune
-   is nonzero, fp_batch_create times each candidate tile shape on the blocks and
-   keeps the fastest per size class; it may run kernels on the blocks' buffers. */
+   replays it.  Unlinked batches with local Lax-Friedrichs speeds are captured as up to
+   four independent chains of the graph, each advancing a group of the blocks of about equal
+   point count, so the chains' launches run side by side on the GPU (then one launch per
+   chain covers that chain's blocks).  A batch runs one CTA shape of the sweep in every
+   direction (fp_get_cta_sizes; the folded FP32 linear-upwind sweep its alternative one),
+   with the blocks' tiles where they are of that shape and the defaults elsewhere.  The
+   batch keeps pointers to the contexts (they must outlive it) and to the caller's state
+   buffers q_devs[b] given at creation.  When autotune is nonzero, fp_batch_create times each
+   candidate tile of that shape on the blocks and keeps the fastest per size class
+   (fp_batch_get_tile); it may run kernels on the blocks' buffers. */
 int fp_batch_create(fp_ctx *const *blocks, int nblocks, void *const *q_devs, int autotune,
                     void *stream, fp_batch **out);
 /* Side `side` (0 = low, 1 = high) of direction `dir` of block `a` (index into the batch's
