@@ -257,8 +257,8 @@ void fp_free(fp_ctx *ctx);                 /* NULL-safe; synchronises the device
    A batch advances many independent blocks (same precision, scheme, metric order)
    together: one persistent launch per direction pass covers the work of every
    block, the three RK stages are captured once into a CUDA graph, and each call
-   replays it.  Unlinked batches with local Lax-Friedrichs speeds are captured as two
-   independent chains of the graph, each advancing a group of the blocks of about equal
+   replays it.  Unlinked batches with local Lax-Friedrichs speeds are captured as up to
+   four independent chains of the graph, each advancing a group of the blocks of about equal
    point count, so the chains' launches run side by side on the GPU (then one launch per
    chain covers that chain's blocks).  A batch runs one CTA shape of the sweep in every
    direction (fp_get_cta_sizes; the folded FP32 linear-upwind sweep its alternative one),

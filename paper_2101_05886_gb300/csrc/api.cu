@@ -69,7 +69,7 @@ struct fp_batch {
   // Graph branches: groups of blocks whose RK steps run as independent chains of the graph,
   // so one group's launches fill the end-of-pass tail of another's.  One branch when blocks
   // are linked (a block reads its neighbours' stage states) or the LF speeds are global.
-  static constexpr int kMaxBranch = 2;
+  static constexpr int kMaxBranch = 4;
   int nbranch = 1;
   int2 *bitems[kMaxBranch][3] = {};
   int bnitems[kMaxBranch][3] = {};

@@ -272,15 +272,17 @@ def test_batch_matches_single_blocks_bitwise(precision):
 
 
 def test_batch_graph_branches_and_launch_counts():
-    """An unlinked batch of two or more blocks with local LF speeds runs its RK step as two
-    graph branches (one launch per branch and direction pass); one block, or global LF speeds
-    (two reduction launches per stage), keep one chain.  The global-LF batch step equals
-    per-block steps bit for bit."""
+    """An unlinked batch of two or more blocks with local LF speeds runs its RK step as up to
+    four graph branches (one launch per branch and direction pass); one block, or global LF
+    speeds (two reduction launches per stage), keep one chain.  The global-LF batch step
+    equals per-block steps bit for bit."""
     grids, qinf, blocks, states = _mini_batch(F32)
-    for n in (4, 2):
-        two = Batch(blocks[:n], states[:n], autotune=False)
-        assert two.launches_per_step() == 2 * 3 * 3
-        two.close()
+    four = Batch(blocks, states, autotune=False)
+    assert len(blocks) == 4 and four.launches_per_step() == 4 * 3 * 3
+    four.close()
+    two = Batch(blocks[:2], states[:2], autotune=False)
+    assert two.launches_per_step() == 2 * 3 * 3
+    two.close()
     one = Batch(blocks[:1], states[:1], autotune=False)
     assert one.launches_per_step() == 3 * 3
     one.close()
@@ -881,7 +883,7 @@ def test_ordered_pipe_sees_host_states_written_by_earlier_stream_work():
 def test_full_size_batched_workload_sampled_parity(scheme):
     """The 64-block batched workload at full size (34.5M points) with the benchmark's autotuned
     tiles and persistent launches (the residual call runs one launch per pass over all blocks;
-    the timed graph runs the same kernel over two groups of the blocks, equal per block bit for
+    the timed graph runs the same kernel over up to four groups of the blocks, equal per block bit for
     bit, see the batch tests): dQ/dt of sampled blocks against the oracle on interior
     sub-boxes next to the low corner, in the middle and next to the high corner.  FP32 on a
     Mach 3 stream with a 1e-3 perturbation (float-rounded state and q_inf on both sides):
