@@ -7,12 +7,10 @@
 
 namespace fpk {
 
-constexpr int kThreads = 256;        // threads of a sweep CTA unless sweep_threads says otherwise
 constexpr int kCellFields = 17;      // per-cell values staged in shared memory
 constexpr int kFaceFields = 10;      // per-face values staged in shared memory (W, delta)
 constexpr int kNextFields = 15;      // staged per thread: next chunk's cell (Q, k, 1/J), face metrics x2
 constexpr int kEpiFields = 13;       // epilogue operands staged per thread (accumulator, Q^n, dk)
-constexpr int kRing = 3 * kThreads;  // shared-memory stride of one staged field (2S slots x TT lines, padded)
 
 // CTA shape of a sweep variant (precision, scheme, fix: 0 switches read at run time, 1 folded,
 // 2 folded with the alternative shape): its threads, which equal faces per chunk x lines per
