@@ -99,6 +99,9 @@ def test_pipe_and_link_calls_reject_null_arguments(lib):
     assert lib.fp_pipe_create(None, 0, None, 4, 0, None) == B.FP_ERR_ARG
     assert lib.fp_pipe_rk3_step_host(None, None, 1e-3, None) == B.FP_ERR_ARG
     assert lib.fp_pipe_set_ordered(None, 1) == B.FP_ERR_ARG
+    a, b = ctypes.c_int(), ctypes.c_int()
+    assert lib.fp_get_cta_sizes(None, ctypes.byref(a), ctypes.byref(b)) == B.FP_ERR_ARG
+    assert lib.fp_batch_get_tile(None, 0, 0, ctypes.byref(a), ctypes.byref(b)) == B.FP_ERR_ARG
     assert lib.fp_pipe_groups(None) == 0
     assert lib.fp_pipe_launches_per_step(None) == 0
     lib.fp_pipe_free(None)
